@@ -244,19 +244,19 @@ def _dot2_bound(n, exact_sum, absum):
 @pytest.mark.parametrize("kind", ["random", "cancel", "positive"])
 def test_dot_exact_small(n, kind):
     g = np.random.default_rng(1000 + n)
-    fx, fy = (1, 5), (0, 3)
+    fx, fy = (1, 7), (1, 8)      # products need more than 53 bits: the error term matters
     xv = g.standard_normal(n) * np.exp2(g.integers(-30, 30, n))
-    yv = g.standard_normal(n).astype(np.float32)
+    yv = g.standard_normal(n)
     if kind == "cancel" and n > 1:
         yv[n // 2:] = -yv[: n - n // 2] if n % 2 == 0 else yv[n // 2:]
         xv[n // 2:] = xv[: n - n // 2] if n % 2 == 0 else xv[n // 2:]
     if kind == "positive":
         xv, yv = np.abs(xv), np.abs(yv)
     xs = oracle.pack(xv, *fx)
-    ys = oracle.pack(yv.astype(np.float32), *fy)
+    ys = oracle.pack(yv, *fy)
     d2, naive, absum = oracle.dot(n, xs, fx, 1, ys, fy, 1)
     xq = [exact.native_value(1, int(b)) for b in oracle.unpack(xs, *fx)]
-    yq = [exact.native_value(0, int(b)) for b in oracle.unpack(ys, *fy)]
+    yq = [exact.native_value(1, int(b)) for b in oracle.unpack(ys, *fy)]
     s = sum((a * b for a, b in zip(xq, yq)), Fraction(0))
     ab = float(sum((abs(a * b) for a, b in zip(xq, yq)), Fraction(0)))
     assert abs(Fraction(d2) - s) <= Fraction(_dot2_bound(n, float(s), ab)) * 1.000001
@@ -279,12 +279,13 @@ def test_dot_strides_vs_numpy(incx, incy):
     assert abs(d2 - ref) <= 2 * n * 2.0 ** -53 * float(np.abs(xv * yv).sum())
 
 
-@pytest.mark.parametrize("base,kx,ky", [(1, 4, 4), (1, 5, 3), (1, 8, 2), (0, 3, 2), (0, 4, 3)])
+@pytest.mark.parametrize("base,kx,ky", [(1, 4, 4), (1, 5, 3), (1, 8, 2), (1, 8, 8), (0, 3, 2),
+                                        (0, 4, 3), (0, 4, 4)])
 @pytest.mark.parametrize("mode", ["rne", "rtz"])
 def test_axpy_exact(base, kx, ky, mode):
     n = 400
     g = np.random.default_rng(300 + kx * 10 + ky)
-    alpha = 1.5 if base == 1 else -0.37
+    alpha = 0.1234567890123 if base == 1 else -0.37   # many bits: alpha*x is inexact
     dt = np.float32 if base == 0 else np.float64
     xs = oracle.pack(g.standard_normal(n).astype(dt), base, kx)
     ys = oracle.pack(g.standard_normal(n).astype(dt), base, ky)
