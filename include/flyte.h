@@ -1,0 +1,166 @@
+/*
+ * flyte.h -- C ABI of the GB300 flyte library (libflyte.so).
+ *
+ * A flyte (Anderson & Gregg, "Vectorization of Multibyte Floating Point Data
+ * Formats", PACT 2016) stores an IEEE-754 value in its top k bytes: the sign
+ * and the full exponent of the next larger built-in type are kept and only
+ * low mantissa bits are dropped (Sec. 3.1, Table 1).  Float-based flytes
+ * widen to binary32 (k = 1..4), double-based ones to binary64 (k = 1..8).
+ * Arrays of flytes are packed back to back, k bytes per element, least
+ * significant byte first (Fig. 1, Sec. 4.1).
+ *
+ * Conventions for every entry point:
+ *  - Data pointers are DEVICE pointers owned by the caller.  The library
+ *    never allocates device memory; scratch space comes from the caller
+ *    (see flyte_workspace_bytes).
+ *  - Calls are asynchronous on `stream` (0 = the legacy default stream) and
+ *    return once the work is enqueued.  No host synchronisation.
+ *  - Strides (inc*, ld*) count ELEMENTS, not bytes, and must be >= 1.
+ *  - A length or dimension of 0 is a no-op returning FLYTE_OK.
+ *  - Argument errors are detected on the host before anything is launched
+ *    and return a status; nothing is written in that case.  CUDA launch
+ *    errors return FLYTE_ERR_CUDA.  flyte_last_error_string() describes the
+ *    last failure of the calling thread.
+ *  - Any pointer alignment is accepted; 16-byte aligned pointers (and, for
+ *    matrices, rows that start on 16-byte boundaries) take the fast paths.
+ *  - Outputs must not overlap inputs, except y in flyte_axpy, which is
+ *    updated in place.
+ */
+#ifndef FLYTE_H
+#define FLYTE_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Native type a flyte widens to (Sec. 3.1: "the next largest built-in type"). */
+typedef enum { FLYTE_F32 = 0, FLYTE_F64 = 1 } flyte_base;
+
+/* Narrowing modes (Sec. 5).
+ *  FLYTE_RNE      round to nearest, ties to even (Sec. 5.2), with IEEE
+ *                 overflow to infinity and gradual underflow (Sec. 5.3).
+ *  FLYTE_RTZ      round toward zero, i.e. truncation (Sec. 5.1); the mode
+ *                 of the paper's experiments (Sec. 6).
+ *  FLYTE_HALF_UP  add half an ULP and truncate (Fig. 6).
+ *  FLYTE_RTO      round to odd (Sec. 7, after Boldo & Melquiond).
+ * In every mode a NaN stays NaN: sign and high payload are kept and the
+ * format's quiet bit is set (Sec. 5.3.4).  For k = 1, which keeps only 7
+ * exponent bits and has no Inf/NaN codes, the magnitude saturates at 0x7F. */
+typedef enum {
+  FLYTE_RNE = 0,
+  FLYTE_RTZ = 1,
+  FLYTE_HALF_UP = 2,
+  FLYTE_RTO = 3
+} flyte_round;
+
+typedef enum {
+  FLYTE_OK = 0,
+  FLYTE_ERR_INVALID_ARG = 1,   /* bad k/base/mode, null pointer, n < 0, stride < 1, lda too small */
+  FLYTE_ERR_UNSUPPORTED = 2,   /* a valid combination this library does not implement */
+  FLYTE_ERR_ALIGNMENT = 3,     /* reserved: an operation that requires an alignment */
+  FLYTE_ERR_CUDA = 4,          /* a CUDA call or launch failed */
+  FLYTE_ERR_WORKSPACE = 5      /* workspace pointer null or smaller than flyte_workspace_bytes() */
+} flyte_status;
+
+/* Format of a flyte operand: k bytes per element, widening to `base`.
+ * Valid: base FLYTE_F32 with k in 1..4, base FLYTE_F64 with k in 1..8
+ * (Table 1 lists 16..32 and 40..64 bits; the other widths follow the same
+ * "top k bytes" rule).  k = 4 (F32) and k = 8 (F64) are the native types. */
+typedef struct {
+  int32_t k;
+  int32_t base; /* flyte_base */
+} flyte_fmt;
+
+/* ---- conversion (Sec. 3-5) ------------------------------------------------ */
+
+/* Pack: dst element i (k bytes at byte (i*inc_dst)*k) = round(src[i*inc_src]).
+ * src: n values of the native type of f.base (float or double), device.
+ * dst: packed k-byte stream, device.  Bit-exact: rounding is done on the
+ * integer pattern (Sec. 5), never through floating-point arithmetic, so NaN
+ * payloads and subnormals are handled exactly.  The GPU writes each output
+ * byte once; elements of different threads never share a store. */
+flyte_status flyte_pack(void* dst, const void* src, int64_t n, flyte_fmt f, int64_t inc_dst,
+                        int64_t inc_src, flyte_round mode, cudaStream_t stream);
+
+/* Unpack: dst[i*inc_dst] (float or double per f.base) = the k-byte element
+ * i*inc_src of src shifted left and padded with zero bits (Fig. 1: the
+ * 24-bit pattern "num << 8"; Sec. 4.1).  Exact, no rounding. */
+flyte_status flyte_unpack(void* dst, const void* src, int64_t n, flyte_fmt f, int64_t inc_dst,
+                          int64_t inc_src, cudaStream_t stream);
+
+/* ---- BLAS level 1 (Sec. 6) --------------------------------------------------- */
+
+/* dot: *result_dev = sum_i x_i * y_i over the unpacked values, accumulated
+ * at least in binary64 (the AT_LEAST rule of Sec. 4.4) whatever the bases.
+ * result_dev: one double in device memory.  ws: device scratch of at least
+ * flyte_workspace_bytes("dot", n, 0, 0, fx) bytes, 16-byte aligned.
+ * Accuracy: |result - exact| <= 4 n 2^-53 sum |x_i y_i| for finite data;
+ * NaN if any term is NaN or infinities of both signs occur, else +-Inf.
+ * Deterministic: the same inputs give the same bits on every call. */
+flyte_status flyte_dot(double* result_dev, int64_t n, const void* x, flyte_fmt fx, int64_t incx,
+                       const void* y, flyte_fmt fy, int64_t incy, void* ws, size_t ws_bytes,
+                       cudaStream_t stream);
+
+/* axpy, in place: y_i <- pack(fma(alpha, x_i, y_i), mode) (FP_CONTRACT on,
+ * Sec. 4.4 and 6).  The fma runs in the formats' native type: binary64 for
+ * double-based, binary32 (alpha rounded to float) for float-based; fx.base
+ * must equal fy.base (else FLYTE_ERR_UNSUPPORTED).  Bit-exact against a
+ * correctly rounded fma followed by the pack of flyte_pack. */
+flyte_status flyte_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, int64_t incx, void* y,
+                        flyte_fmt fy, int64_t incy, flyte_round mode, cudaStream_t stream);
+
+/* ---- BLAS level 2 (Sec. 6.3.2) ----------------------------------------------- */
+
+/* gemv on a row-major k-byte matrix A (m rows, n columns, row i starts at
+ * element i*lda, lda >= n):
+ *   trans 'N': y_i <- alpha * sum_j A_ij x_j + beta * y_i,   i < m, x has n entries
+ *   trans 'T': y_j <- alpha * sum_i A_ij x_i + beta * y_j,   j < n, x has m entries
+ * x, y: binary64 device vectors with strides incx, incy.  Sums are formed
+ * to binary64 accuracy; the epilogue is fma(alpha, t, beta * y).  BLAS quick
+ * returns: beta == 0 means y is not read; alpha == 0 means A and x are not
+ * read.  Accuracy: |y - y_exact| <= 4 (len + 2) 2^-53 (|alpha| sum |A x| + |beta y|).
+ * ws: scratch of flyte_workspace_bytes("gemv_n" or "gemv_t", m, n, 0, fa) bytes. */
+flyte_status flyte_gemv(char trans, int64_t m, int64_t n, double alpha, const void* A, flyte_fmt fa,
+                        int64_t lda, const double* x, int64_t incx, double beta, double* y,
+                        int64_t incy, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---- BLAS level 3 (Sec. 6.3.3) ----------------------------------------------- */
+
+/* gemm, row-major: C <- alpha * A B + beta * C with A m x k_ (lda >= k_),
+ * B k_ x n (ldb >= n), C m x n (ldc >= n).  fa and fb must be equal.
+ *   float-based k = 2: codes are bfloat16 bit patterns, tensor cores, FP32 accumulation
+ *   float-based k = 3: each value split exactly into two bfloat16 terms, all
+ *                      four cross products on tensor cores, FP32 accumulation
+ *   float-based k = 4: binary32 inputs split into three bfloat16 terms
+ *   double-based k >= 2: binary64 tensor-core (DMMA) products, binary64 C
+ *   float-based k = 1: FLYTE_ERR_UNSUPPORTED
+ * C is float for float-based formats and double for double-based ones.
+ * Accuracy (float-based): |C - C_exact| <= 2^-22 (|alpha| sum_l |A_il B_lj| + |beta C_ij|);
+ * (double-based): 4 k_ 2^-53 (same sums).  beta == 0: C is not read. */
+flyte_status flyte_gemm(int64_t m, int64_t n, int64_t k_, double alpha, const void* A, flyte_fmt fa,
+                        int64_t lda, const void* B, flyte_fmt fb, int64_t ldb, double beta, void* C,
+                        int64_t ldc, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* ---- helpers ---------------------------------------------------------------- */
+
+/* Scratch bytes an operation needs for the given sizes: op is "dot",
+ * "gemv_n", "gemv_t" or "gemm" (m, n, k_ as in that call; unused ones 0).
+ * Returns 0 for an operation that needs none and (size_t)-1 for an unknown
+ * op.  The amount depends only on the arguments, never on the device. */
+size_t flyte_workspace_bytes(const char* op, int64_t m, int64_t n, int64_t k_, flyte_fmt f);
+
+/* Description of the last failure on the calling host thread ("" if none). */
+const char* flyte_last_error_string(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int flyte_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLYTE_H */

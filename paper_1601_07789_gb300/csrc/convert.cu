@@ -1,0 +1,241 @@
+// convert.cu -- streaming pack and unpack of flyte arrays (Sec. 3-5 of the paper).
+//
+// Fast path (unit strides, suitably aligned pointers): each thread owns
+// groups of 4 consecutive elements.  4 elements of k bytes are 4k bytes, a
+// whole number of 32-bit words, so a thread reads (unpack) or writes (pack)
+// its packed bytes with aligned vector accesses that never overlap another
+// thread's: the GPU form of the paper's "compact, blend, then
+// non-overlapping stores" (Sec. 4.3).  Inside the thread the bytes are split
+// into lanes with funnel shifts (Sec. 4.1: shift and pad with zeros) or
+// assembled from the rounded codes.  Native values move as 16-byte vectors.
+// Each thread keeps UNROLL groups in flight to cover HBM latency.
+//
+// Generic path (any stride or alignment): one thread per element with byte
+// loads and stores; elements never share a byte, so byte stores from
+// different threads cannot conflict.
+#include "flyte_internal.cuh"
+
+namespace flyte {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kUnroll = 4;
+
+// Widest power-of-two access (<= 16 bytes) that divides a 4k-byte group.
+template <int K>
+__host__ __device__ constexpr int group_access_bytes() {
+  return (4 * K) % 16 == 0 ? 16 : ((4 * K) % 8 == 0 ? 8 : 4);
+}
+
+template <int K>
+__device__ __forceinline__ void load_group(const uint8_t* p, uint32_t (&w)[K]) {
+  constexpr int S = group_access_bytes<K>();
+  if constexpr (S == 16) {
+#pragma unroll
+    for (int i = 0; i < K / 4; ++i) {
+      uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + i);
+      w[4 * i] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
+    }
+  } else if constexpr (S == 8) {
+#pragma unroll
+    for (int i = 0; i < K / 2; ++i) {
+      uint2 v = __ldg(reinterpret_cast<const uint2*>(p) + i);
+      w[2 * i] = v.x; w[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < K; ++i) w[i] = __ldg(reinterpret_cast<const uint32_t*>(p) + i);
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void store_group(uint8_t* p, const uint32_t (&w)[K]) {
+  constexpr int S = group_access_bytes<K>();
+  if constexpr (S == 16) {
+#pragma unroll
+    for (int i = 0; i < K / 4; ++i)
+      reinterpret_cast<uint4*>(p)[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+  } else if constexpr (S == 8) {
+#pragma unroll
+    for (int i = 0; i < K / 2; ++i) reinterpret_cast<uint2*>(p)[i] = make_uint2(w[2 * i], w[2 * i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < K; ++i) reinterpret_cast<uint32_t*>(p)[i] = w[i];
+  }
+}
+
+// 4 native values: 16 bytes (float) or 32 bytes (double).
+template <int BASE>
+struct Quad {
+  typename Native<BASE>::bits v[4];
+};
+
+template <int BASE>
+__device__ __forceinline__ void load_quad(const void* p, Quad<BASE>& q) {
+  if constexpr (BASE == FLYTE_F32) {
+    uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+    q.v[0] = a.x; q.v[1] = a.y; q.v[2] = a.z; q.v[3] = a.w;
+  } else {
+    const uint4* s = reinterpret_cast<const uint4*>(p);
+    uint4 a = __ldg(s), b = __ldg(s + 1);
+    q.v[0] = (uint64_t(a.y) << 32) | a.x; q.v[1] = (uint64_t(a.w) << 32) | a.z;
+    q.v[2] = (uint64_t(b.y) << 32) | b.x; q.v[3] = (uint64_t(b.w) << 32) | b.z;
+  }
+}
+
+template <int BASE>
+__device__ __forceinline__ void store_quad(void* p, const Quad<BASE>& q) {
+  if constexpr (BASE == FLYTE_F32) {
+    *reinterpret_cast<uint4*>(p) = make_uint4(q.v[0], q.v[1], q.v[2], q.v[3]);
+  } else {
+    uint4* d = reinterpret_cast<uint4*>(p);
+    d[0] = make_uint4(uint32_t(q.v[0]), uint32_t(q.v[0] >> 32), uint32_t(q.v[1]), uint32_t(q.v[1] >> 32));
+    d[1] = make_uint4(uint32_t(q.v[2]), uint32_t(q.v[2] >> 32), uint32_t(q.v[3]), uint32_t(q.v[3] >> 32));
+  }
+}
+
+// ---- unpack ------------------------------------------------------------------
+
+template <int BASE, int K>
+__global__ void __launch_bounds__(kThreads) unpack_groups(const uint8_t* __restrict__ src,
+                                                          void* __restrict__ dst, int64_t ngroups) {
+  using Bits = typename Native<BASE>::bits;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (; g < ngroups; g += kUnroll * stride) {
+    uint32_t w[kUnroll][K];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t gu = g + u * stride;
+      if (gu < ngroups) load_group<K>(src + gu * (4 * K), w[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t gu = g + u * stride;
+      if (gu < ngroups) {
+        Quad<BASE> q;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) q.v[e] = extract_widened<BASE, K>(w[u], e);
+        store_quad<BASE>(static_cast<uint8_t*>(dst) + gu * (4 * sizeof(Bits)), q);
+      }
+    }
+  }
+}
+
+template <int BASE, int K>
+__global__ void __launch_bounds__(kThreads) unpack_generic(const uint8_t* __restrict__ src, int64_t inc_src,
+                                                           void* __restrict__ dst, int64_t inc_dst,
+                                                           int64_t first, int64_t n) {
+  using Bits = typename Native<BASE>::bits;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = first + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t q = load_code_bytes<K>(src + i * inc_src * K);
+    const Bits u = widen<BASE, K>(q);
+    uint8_t* d = static_cast<uint8_t*>(dst) + i * inc_dst * int64_t(sizeof(Bits));
+    if ((reinterpret_cast<uintptr_t>(d) & (sizeof(Bits) - 1)) == 0) {
+      *reinterpret_cast<Bits*>(d) = u;
+    } else {
+#pragma unroll
+      for (int b = 0; b < int(sizeof(Bits)); ++b) d[b] = uint8_t(u >> (8 * b));
+    }
+  }
+}
+
+// ---- pack --------------------------------------------------------------------
+
+template <int BASE, int K>
+__global__ void __launch_bounds__(kThreads) pack_groups(const void* __restrict__ src, uint8_t* __restrict__ dst,
+                                                        int64_t ngroups, int mode) {
+  using Bits = typename Native<BASE>::bits;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (; g < ngroups; g += kUnroll * stride) {
+    Quad<BASE> q[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t gu = g + u * stride;
+      if (gu < ngroups) load_quad<BASE>(static_cast<const uint8_t*>(src) + gu * (4 * sizeof(Bits)), q[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t gu = g + u * stride;
+      if (gu < ngroups) {
+        uint32_t w[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) w[j] = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) deposit_code<K>(w, e, narrow<BASE, K>(q[u].v[e], mode));
+        store_group<K>(dst + gu * (4 * K), w);
+      }
+    }
+  }
+}
+
+template <int BASE, int K>
+__global__ void __launch_bounds__(kThreads) pack_generic(const void* __restrict__ src, int64_t inc_src,
+                                                         uint8_t* __restrict__ dst, int64_t inc_dst,
+                                                         int64_t first, int64_t n, int mode) {
+  using Bits = typename Native<BASE>::bits;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = first + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint8_t* s = static_cast<const uint8_t*>(src) + i * inc_src * int64_t(sizeof(Bits));
+    Bits u = 0;
+    if ((reinterpret_cast<uintptr_t>(s) & (sizeof(Bits) - 1)) == 0) {
+      u = *reinterpret_cast<const Bits*>(s);
+    } else {
+#pragma unroll
+      for (int b = int(sizeof(Bits)) - 1; b >= 0; --b) u = (u << 8) | Bits(s[b]);
+    }
+    store_code_bytes<K>(dst + i * inc_dst * K, narrow<BASE, K>(u, mode));
+  }
+}
+
+bool aligned(const void* p, int bytes) { return (reinterpret_cast<uintptr_t>(p) % bytes) == 0; }
+
+}  // namespace
+
+flyte_status launch_unpack(void* dst, const void* src, int64_t n, flyte_fmt f, int64_t inc_dst,
+                           int64_t inc_src, cudaStream_t s) {
+  return dispatch_fmt(f, [&]<int BASE, int K>() -> flyte_status {
+    using Bits = typename Native<BASE>::bits;
+    int64_t first = 0;
+    const bool fast = inc_src == 1 && inc_dst == 1 && aligned(src, group_access_bytes<K>()) && aligned(dst, 16);
+    if (fast && n >= 4) {
+      const int64_t ngroups = n / 4;
+      unpack_groups<BASE, K><<<grid_for(ngroups, kThreads * kUnroll), kThreads, 0, s>>>(
+          static_cast<const uint8_t*>(src), dst, ngroups);
+      FLYTE_TRY_LAUNCH("unpack");
+      first = ngroups * 4;
+    }
+    if (first < n) {
+      unpack_generic<BASE, K><<<grid_for(n - first, kThreads), kThreads, 0, s>>>(
+          static_cast<const uint8_t*>(src), inc_src, dst, inc_dst, first, n);
+      FLYTE_TRY_LAUNCH("unpack");
+    }
+    (void)sizeof(Bits);
+    return FLYTE_OK;
+  });
+}
+
+flyte_status launch_pack(void* dst, const void* src, int64_t n, flyte_fmt f, int64_t inc_dst,
+                         int64_t inc_src, int mode, cudaStream_t s) {
+  return dispatch_fmt(f, [&]<int BASE, int K>() -> flyte_status {
+    int64_t first = 0;
+    const bool fast = inc_src == 1 && inc_dst == 1 && aligned(src, 16) && aligned(dst, group_access_bytes<K>());
+    if (fast && n >= 4) {
+      const int64_t ngroups = n / 4;
+      pack_groups<BASE, K><<<grid_for(ngroups, kThreads * kUnroll), kThreads, 0, s>>>(
+          src, static_cast<uint8_t*>(dst), ngroups, mode);
+      FLYTE_TRY_LAUNCH("pack");
+      first = ngroups * 4;
+    }
+    if (first < n) {
+      pack_generic<BASE, K><<<grid_for(n - first, kThreads), kThreads, 0, s>>>(
+          src, inc_src, static_cast<uint8_t*>(dst), inc_dst, first, n, mode);
+      FLYTE_TRY_LAUNCH("pack");
+    }
+    return FLYTE_OK;
+  });
+}
+
+}  // namespace flyte

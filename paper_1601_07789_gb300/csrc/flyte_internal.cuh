@@ -1,0 +1,247 @@
+// flyte_internal.cuh -- shared definitions of the CUDA library (not part of the ABI).
+//
+// Format traits, the bit-exact narrowing of Sec. 5 written on integer
+// patterns, and the byte-stream helpers of Sec. 4 used by every kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/flyte.h"
+
+namespace flyte {
+
+// ---- status plumbing -------------------------------------------------------
+
+void set_error(const char* fmt, ...);
+flyte_status cuda_status(cudaError_t e, const char* what);
+
+#define FLYTE_TRY_LAUNCH(what)                                   \
+  do {                                                           \
+    cudaError_t _e = cudaGetLastError();                         \
+    if (_e != cudaSuccess) return ::flyte::cuda_status(_e, what); \
+  } while (0)
+
+// ---- format traits (Sec. 3.1, Table 1) ------------------------------------
+
+template <int BASE>
+struct Native;
+template <>
+struct Native<FLYTE_F32> {
+  using bits = uint32_t;
+  using value = float;
+  static constexpr int W = 32;        // native width in bits
+  static constexpr int E = 8;         // exponent bits, same as the built-in type
+};
+template <>
+struct Native<FLYTE_F64> {
+  using bits = uint64_t;
+  using value = double;
+  static constexpr int W = 64;
+  static constexpr int E = 11;
+};
+
+template <int BASE, int K>
+struct Fmt {
+  using N = Native<BASE>;
+  using bits = typename N::bits;
+  static constexpr int W = N::W;
+  static constexpr int E = N::E;
+  static constexpr int D = W - 8 * K;                 // dropped low bits
+  static constexpr bits SIGN = bits(1) << (W - 1);
+  static constexpr bits MAG = SIGN - 1;
+  static constexpr bits INF = ((bits(1) << E) - 1) << (W - 1 - E);
+  static constexpr uint64_t CODE_SIGN = uint64_t(1) << (8 * K - 1);
+  // quiet bit of the flyte: its most significant mantissa bit (K >= 2)
+  static constexpr uint64_t QUIET = K >= 2 ? (uint64_t(1) << (8 * K - 2 - E)) : 0;
+};
+
+// ---- narrowing (Sec. 5), integer-only -----------------------------------
+//
+// Every mode works on the magnitude m = |u| as an unsigned integer.  NaNs
+// are recognised first (m > INF), keep their high payload and get the quiet
+// bit.  Nearest-even uses the bias form t = (m + half - 1 + lsb) >> D, which
+// carries into the exponent exactly when IEEE rounding does (Sec. 5.3).
+// k = 1 has no Inf/NaN codes: specials map to 0x7F and the magnitude is
+// clamped at 0x7F.
+
+template <int BASE, int K>
+__device__ __forceinline__ uint64_t narrow(typename Fmt<BASE, K>::bits u, int mode) {
+  using F = Fmt<BASE, K>;
+  using B = typename F::bits;
+  if constexpr (F::D == 0) {
+    return uint64_t(u);
+  } else {
+    const B m = u & F::MAG;
+    const uint64_t s = (u & F::SIGN) ? F::CODE_SIGN : 0;
+    const B half = B(1) << (F::D - 1);
+    const B kept = m >> F::D;
+    B t;
+    if (mode == FLYTE_RNE) {
+      t = (m + (half - 1) + (kept & 1)) >> F::D;
+    } else if (mode == FLYTE_RTZ) {
+      t = kept;
+    } else if (mode == FLYTE_HALF_UP) {
+      t = (m + half) >> F::D;
+    } else {  // FLYTE_RTO
+      t = kept | B((m & ((half << 1) - 1)) != 0);
+    }
+    if constexpr (K == 1) {
+      if (m >= F::INF) t = 0x7F;
+      t = t > B(0x7F) ? B(0x7F) : t;
+    } else {
+      if (m > F::INF) t = kept | B(F::QUIET);
+    }
+    return s | uint64_t(t);
+  }
+}
+
+template <int BASE, int K>
+__device__ __forceinline__ typename Fmt<BASE, K>::bits widen(uint64_t q) {
+  using F = Fmt<BASE, K>;
+  return typename F::bits(q) << F::D;
+}
+
+// ---- byte buffers held in 32-bit registers (Sec. 4.1, 4.3) --------------------
+//
+// A group of G consecutive elements occupies G*K bytes = NW words.  get4<P>()
+// returns bytes [P, P+4) of the buffer (bytes outside read as zero); the
+// positions are compile-time constants after unrolling, so this lowers to
+// one funnel shift or a register move.
+
+template <int NW>
+__device__ __forceinline__ uint32_t word_at(const uint32_t (&w)[NW], int i) {
+  return (i < 0 || i >= NW) ? 0u : w[i];
+}
+
+template <int NW>
+__device__ __forceinline__ uint32_t get4(const uint32_t (&w)[NW], int pos) {
+  const int wi = pos >= 0 ? pos / 4 : -((-pos + 3) / 4);
+  const int r = pos - 4 * wi;
+  const uint32_t lo = word_at(w, wi);
+  if (r == 0) return lo;
+  const uint32_t hi = word_at(w, wi + 1);
+  return __funnelshift_r(lo, hi, 8 * r);
+}
+
+// Element e of a K-byte group buffer, returned as its native bit pattern
+// (the code shifted up by D bits: the zero padding of Fig. 1).
+template <int BASE, int K, int NW>
+__device__ __forceinline__ typename Fmt<BASE, K>::bits extract_widened(const uint32_t (&w)[NW], int e) {
+  using F = Fmt<BASE, K>;
+  constexpr int NB = F::W / 8;                 // native bytes
+  const int p = e * K + K - NB;                // buffer position of the native's byte 0
+  if constexpr (BASE == FLYTE_F32) {
+    uint32_t v = get4(w, p);
+    if constexpr (F::D > 0) v &= ~((1u << F::D) - 1u);
+    return v;
+  } else {
+    uint32_t lo = get4(w, p);
+    uint32_t hi = get4(w, p + 4);
+    if constexpr (F::D >= 32) {
+      lo = 0;
+      if constexpr (F::D > 32) hi &= ~((1u << (F::D - 32)) - 1u);
+    } else if constexpr (F::D > 0) {
+      lo &= ~((1u << F::D) - 1u);
+    }
+    return (uint64_t(hi) << 32) | lo;
+  }
+}
+
+// Element e of the buffer as its raw K-byte code (low 8K bits).
+template <int K, int NW>
+__device__ __forceinline__ uint64_t extract_code(const uint32_t (&w)[NW], int e) {
+  const int p = e * K;
+  uint64_t lo = get4(w, p);
+  if constexpr (K <= 4) {
+    return K == 4 ? lo : (lo & ((uint64_t(1) << (8 * K)) - 1));
+  } else {
+    uint64_t hi = get4(w, p + 4);
+    uint64_t v = lo | (hi << 32);
+    return K == 8 ? v : (v & ((uint64_t(1) << (8 * K)) - 1));
+  }
+}
+
+// OR code c (low 8K bits) into the buffer at element e.
+template <int K, int NW>
+__device__ __forceinline__ void deposit_code(uint32_t (&w)[NW], int e, uint64_t c) {
+  const int p = e * K;  // first byte
+#pragma unroll
+  for (int j = 0; j < NW; ++j) {
+    const int off = p - 4 * j;  // byte offset of the code relative to word j
+    if (off >= 4 || off + K <= 0) continue;
+    if (off >= 0) {
+      w[j] |= uint32_t(c << (8 * off));
+    } else {
+      w[j] |= uint32_t(c >> (8 * (-off)));
+    }
+  }
+}
+
+// ---- scalar byte access for the generic (any stride / alignment) paths ----------
+
+template <int K>
+__device__ __forceinline__ uint64_t load_code_bytes(const uint8_t* p) {
+  uint64_t q = 0;
+#pragma unroll
+  for (int b = K - 1; b >= 0; --b) q = (q << 8) | uint64_t(p[b]);
+  return q;
+}
+
+template <int K>
+__device__ __forceinline__ void store_code_bytes(uint8_t* p, uint64_t q) {
+#pragma unroll
+  for (int b = 0; b < K; ++b) p[b] = uint8_t(q >> (8 * b));
+}
+
+// ---- launch geometry -----------------------------------------------------------
+
+int sm_count();   // streaming multiprocessors of the current device (cached per device)
+
+inline unsigned grid_for(int64_t work_items, int per_block, int max_blocks_per_sm = 8) {
+  int64_t blocks = (work_items + per_block - 1) / per_block;
+  int64_t cap = int64_t(sm_count()) * max_blocks_per_sm;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return unsigned(blocks);
+}
+
+// ---- format dispatch -------------------------------------------------------------
+
+// Calls f.template operator()<BASE, K>() for the runtime (base, k).
+template <typename Fn>
+flyte_status dispatch_fmt(flyte_fmt f, Fn&& fn) {
+  if (f.base == FLYTE_F32) {
+    switch (f.k) {
+      case 1: return fn.template operator()<FLYTE_F32, 1>();
+      case 2: return fn.template operator()<FLYTE_F32, 2>();
+      case 3: return fn.template operator()<FLYTE_F32, 3>();
+      case 4: return fn.template operator()<FLYTE_F32, 4>();
+    }
+  } else {
+    switch (f.k) {
+      case 1: return fn.template operator()<FLYTE_F64, 1>();
+      case 2: return fn.template operator()<FLYTE_F64, 2>();
+      case 3: return fn.template operator()<FLYTE_F64, 3>();
+      case 4: return fn.template operator()<FLYTE_F64, 4>();
+      case 5: return fn.template operator()<FLYTE_F64, 5>();
+      case 6: return fn.template operator()<FLYTE_F64, 6>();
+      case 7: return fn.template operator()<FLYTE_F64, 7>();
+      case 8: return fn.template operator()<FLYTE_F64, 8>();
+    }
+  }
+  return FLYTE_ERR_INVALID_ARG;
+}
+
+inline bool valid_fmt(flyte_fmt f) {
+  return (f.base == FLYTE_F32 && f.k >= 1 && f.k <= 4) || (f.base == FLYTE_F64 && f.k >= 1 && f.k <= 8);
+}
+
+// ---- launchers (one per operation, defined in the kernel files) ---------------------
+
+flyte_status launch_pack(void* dst, const void* src, int64_t n, flyte_fmt f, int64_t inc_dst,
+                         int64_t inc_src, int mode, cudaStream_t s);
+flyte_status launch_unpack(void* dst, const void* src, int64_t n, flyte_fmt f, int64_t inc_dst,
+                           int64_t inc_src, cudaStream_t s);
+
+}  // namespace flyte

@@ -1,0 +1,66 @@
+"""The C-ABI library loads on any machine and exports every declared entry point.
+
+CPU-only: no call here launches GPU work.  Argument errors are rejected on
+the host before anything is launched, so they can be checked without a GPU.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1601_07789_gb300 import build, flyte
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols() -> set[str]:
+    text = open(os.path.join(ROOT, "include", "flyte.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return set(re.findall(r"\b(flyte_[a-z_0-9]+)\s*\(", text))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return flyte.lib()
+
+
+def test_header_declares_the_boundary():
+    assert declared_symbols() == set(flyte.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_version(lib):
+    assert lib.flyte_version() >= 100
+
+
+@pytest.mark.parametrize("k,base", [(0, 0), (5, 0), (9, 1), (2, 7), (-1, 1)])
+def test_bad_format_rejected_on_host(lib, k, base):
+    st = lib.flyte_pack(None, None, 10, flyte.Fmt(k, base), 1, 1, 0, None)
+    assert st == 1
+    assert b"format" in lib.flyte_last_error_string()
+    assert lib.flyte_unpack(None, None, 10, flyte.Fmt(k, base), 1, 1, None) == 1
+
+
+def test_bad_sizes_strides_modes_rejected_on_host(lib):
+    f = flyte.Fmt(3, 1)
+    assert lib.flyte_pack(None, None, -1, f, 1, 1, 0, None) == 1
+    assert lib.flyte_pack(None, None, 10, f, 0, 1, 0, None) == 1
+    assert lib.flyte_pack(None, None, 10, f, 1, -2, 0, None) == 1
+    assert lib.flyte_pack(None, None, 10, f, 1, 1, 9, None) == 1
+    assert lib.flyte_pack(None, None, 10, f, 1, 1, 0, None) == 1      # null pointers
+    assert lib.flyte_unpack(None, None, 10, f, 1, 1, None) == 1
+
+
+def test_zero_length_is_a_noop(lib):
+    f = flyte.Fmt(3, 1)
+    assert lib.flyte_pack(None, None, 0, f, 1, 1, 0, None) == 0
+    assert lib.flyte_unpack(None, None, 0, f, 1, 1, None) == 0
