@@ -241,12 +241,19 @@ static void two_prod(double a, double b, double *p, double *e)
     *p = x;
 }
 
-/* Dot2: the dot product computed as if in twice the working precision. */
+/* Dot2: the dot product computed as if in twice the working precision.
+ * The error-free transformations are only defined for finite terms (the
+ * TwoProduct of an infinity yields inf - inf = NaN), so when any product is
+ * Inf or NaN the plain binary64 sum is returned instead: NaN if a term is
+ * NaN or infinities of both signs occur, else the signed infinity, as the
+ * special-value rules of Sec. 5.3 require. */
 static double dot2(int64_t n, const double *x, const double *y, double *naive, double *absum)
 {
     double p = 0.0, s = 0.0, nv = 0.0, ab = 0.0;
+    int finite = 1;
     for (int64_t i = 0; i < n; ++i) {
         double h, r, q;
+        if (!isfinite(x[i] * y[i])) finite = 0;
         two_prod(x[i], y[i], &h, &r);
         two_sum(p, h, &p, &q);
         s = s + (q + r);
@@ -255,7 +262,7 @@ static double dot2(int64_t n, const double *x, const double *y, double *naive, d
     }
     if (naive) *naive = nv;
     if (absum) *absum = ab;
-    return p + s;
+    return finite ? p + s : nv;
 }
 
 /* ---- dot (BLAS level 1; accumulation AT_LEAST the flyte, Sec. 4.4) ------ */

@@ -373,3 +373,21 @@ def test_gemm_entries_vs_numpy(fa, fb):
     out, absum = oracle.gemm_entries(rows.reshape(-1), cols.reshape(-1), K, 1.0, A, fa, K, B, fb, N)
     assert np.allclose(out.reshape(M, N), ref, rtol=0, atol=4 * K * 2.0 ** -53 * float(absum.max()))
     assert np.allclose(absum.reshape(M, N), np.abs(Av) @ np.abs(Bv), rtol=1e-13)
+
+
+def test_dot_and_gemv_special_value_classes():
+    """Sec. 5.3: an infinite term gives a signed infinity, infinities of both
+    signs or a NaN term give NaN (the error-free transforms are not applied)."""
+    f = (1, 8)
+    def d(vals_x, vals_y):
+        xs = oracle.pack(np.array(vals_x, dtype=np.float64), *f)
+        ys = oracle.pack(np.array(vals_y, dtype=np.float64), *f)
+        return oracle.dot(len(vals_x), xs, f, 1, ys, f, 1)[0]
+    assert d([1.0, np.inf, 2.0], [1.0, 1.0, 1.0]) == np.inf
+    assert d([1.0, np.inf, 2.0], [1.0, -1.0, 1.0]) == -np.inf
+    assert np.isnan(d([1.0, np.inf, np.inf], [1.0, 1.0, -1.0]))
+    assert np.isnan(d([1.0, np.nan, 2.0], [1.0, 1.0, 1.0]))
+    assert np.isnan(d([0.0, np.inf], [np.inf, 0.0]))           # 0 * Inf
+    A = oracle.pack(np.array([1.0, np.inf, 3.0, 4.0]), *f)
+    y, _ = oracle.gemv("N", 2, 2, 1.0, A, f, 2, np.array([1.0, 1.0]), 1, 0.0, np.zeros(2), 1)
+    assert y[0] == np.inf and y[1] == 7.0
