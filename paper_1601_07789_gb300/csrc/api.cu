@@ -79,29 +79,45 @@ flyte_status flyte_dot(double* result_dev, int64_t n, const void* x, flyte_fmt f
                        const void* y, flyte_fmt fy, int64_t incy, void* ws, size_t ws_bytes,
                        cudaStream_t stream) {
   g_error[0] = 0;
-  (void)result_dev; (void)n; (void)x; (void)fx; (void)incx; (void)y; (void)fy; (void)incy;
-  (void)ws; (void)ws_bytes; (void)stream;
-  set_error("dot: not implemented yet");
-  return FLYTE_ERR_UNSUPPORTED;
+  if (!valid_fmt(fx) || !valid_fmt(fy)) return invalid("format (k, base)");
+  if (n < 0) return invalid("n < 0");
+  if (incx < 1 || incy < 1) return invalid("stride < 1");
+  if (!result_dev) return invalid("null result");
+  if (n > 0 && (!x || !y)) return invalid("null x or y");
+  return launch_dot(result_dev, n, x, fx, incx, y, fy, incy, ws, ws_bytes, stream);
 }
 
 flyte_status flyte_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, int64_t incx, void* y,
                         flyte_fmt fy, int64_t incy, flyte_round mode, cudaStream_t stream) {
   g_error[0] = 0;
-  (void)n; (void)alpha; (void)x; (void)fx; (void)incx; (void)y; (void)fy; (void)incy; (void)mode;
-  (void)stream;
-  set_error("axpy: not implemented yet");
-  return FLYTE_ERR_UNSUPPORTED;
+  if (!valid_fmt(fx) || !valid_fmt(fy)) return invalid("format (k, base)");
+  if (fx.base != fy.base) {
+    set_error("axpy: x and y must share the base type");
+    return FLYTE_ERR_UNSUPPORTED;
+  }
+  if (int(mode) < FLYTE_RNE || int(mode) > FLYTE_RTO) return invalid("rounding mode");
+  if (n < 0) return invalid("n < 0");
+  if (incx < 1 || incy < 1) return invalid("stride < 1");
+  if (n == 0) return FLYTE_OK;
+  if (!x || !y) return invalid("null pointer");
+  return launch_axpy(n, alpha, x, fx, incx, y, fy, incy, int(mode), stream);
 }
 
 flyte_status flyte_gemv(char trans, int64_t m, int64_t n, double alpha, const void* A, flyte_fmt fa,
                         int64_t lda, const double* x, int64_t incx, double beta, double* y,
                         int64_t incy, void* ws, size_t ws_bytes, cudaStream_t stream) {
   g_error[0] = 0;
-  (void)trans; (void)m; (void)n; (void)alpha; (void)A; (void)fa; (void)lda; (void)x; (void)incx;
-  (void)beta; (void)y; (void)incy; (void)ws; (void)ws_bytes; (void)stream;
-  set_error("gemv: not implemented yet");
-  return FLYTE_ERR_UNSUPPORTED;
+  if (trans == 'n') trans = 'N';
+  if (trans == 't') trans = 'T';
+  if (trans != 'N' && trans != 'T') return invalid("trans must be 'N' or 'T'");
+  if (!valid_fmt(fa)) return invalid("format (k, base)");
+  if (m < 0 || n < 0) return invalid("m < 0 or n < 0");
+  if (lda < (n > 1 ? n : 1)) return invalid("lda < max(1, n)");
+  if (incx < 1 || incy < 1) return invalid("stride < 1");
+  if (m == 0 || n == 0) return FLYTE_OK;
+  if (!y) return invalid("null y");
+  if (alpha != 0.0 && (!A || !x)) return invalid("null A or x");
+  return launch_gemv(trans, m, n, alpha, A, fa, lda, x, incx, beta, y, incy, ws, ws_bytes, stream);
 }
 
 flyte_status flyte_gemm(int64_t m, int64_t n, int64_t k_, double alpha, const void* A, flyte_fmt fa,
@@ -115,8 +131,11 @@ flyte_status flyte_gemm(int64_t m, int64_t n, int64_t k_, double alpha, const vo
 }
 
 size_t flyte_workspace_bytes(const char* op, int64_t m, int64_t n, int64_t k_, flyte_fmt f) {
-  (void)m; (void)n; (void)k_; (void)f;
-  if (!op) return size_t(-1);
+  (void)k_;
+  if (!op || m < 0 || n < 0 || k_ < 0) return size_t(-1);
+  if (std::strcmp(op, "dot") == 0) return dot_workspace_bytes(n);
+  if (std::strcmp(op, "gemv_n") == 0) return gemv_workspace_bytes('N', m, n, f);
+  if (std::strcmp(op, "gemv_t") == 0) return gemv_workspace_bytes('T', m, n, f);
   return size_t(-1);
 }
 

@@ -1,0 +1,253 @@
+// blas1.cu -- dot and axpy on k-byte streams (Sec. 6, BLAS level 1).
+//
+// dot: both operands are flytes.  Each thread walks 4-element groups of the
+// two streams (grid-stride), widens them in registers and, when all eight
+// values are inside the binary32 window, folds the exact double-word
+// products into 4 double-word accumulators (dwacc.cuh); a group with any
+// other value (zero, subnormal, huge, Inf, NaN) goes into a binary64 FMA
+// accumulator instead, which keeps IEEE Inf/NaN semantics.  Per-block sums go
+// to the workspace and a one-block kernel adds them in a fixed order, so the
+// result is the same on every call.
+//
+// axpy: y <- pack(fma(alpha, x, y)) in place, group by group.  The fma runs in
+// the native type (binary64 or binary32) so it is correctly rounded, and the
+// narrowing is the integer rounding of flyte_pack: the result is bit-exact.
+// Each thread reads and rewrites its own aligned 4k-byte group of y, so the
+// in-place update never has two threads touch the same bytes.
+#include "dwacc.cuh"
+
+namespace flyte {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kDotMaxBlocks = 2048;   // fixed, so the workspace size does not depend on the device
+constexpr int kHdrBytes = 256;
+
+template <int BASE, int K>
+__device__ __forceinline__ bool to_pair(typename Native<BASE>::bits u, float& hi, float& lo) {
+  if constexpr (BASE == FLYTE_F64) {
+    return dbl_to_pair<K>(uint32_t(u >> 32), uint32_t(u), hi, lo);
+  } else {
+    hi = __uint_as_float(u);
+    lo = 0.f;
+    return flt_in_window(u);
+  }
+}
+
+template <int BASE, int K>
+__device__ __forceinline__ double bits_to_double(typename Native<BASE>::bits u) {
+  if constexpr (BASE == FLYTE_F64) {
+    return __longlong_as_double((long long)u);
+  } else {
+    return double(__uint_as_float(u));
+  }
+}
+
+template <int BASE, int K>
+__global__ void __launch_bounds__(kThreads) dot_groups(const uint8_t* __restrict__ X, const uint8_t* __restrict__ Y,
+                                                       int64_t ngrp, int64_t n, int fast,
+                                                       double* __restrict__ partial) {
+  __shared__ double smem[kThreads / 32];
+  DW acc[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) dw_zero(acc[e]);
+  double acc64 = 0.0;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (int64_t g = tid; g < ngrp; g += stride) {
+    uint32_t wx[K], wy[K];
+    load_group<K>(X + g * (4 * K), wx);
+    load_group<K>(Y + g * (4 * K), wy);
+    typename Native<BASE>::bits ux[4], uy[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ux[e] = extract_widened<BASE, K>(wx, e);
+      uy[e] = extract_widened<BASE, K>(wy, e);
+    }
+    bool ok = fast != 0;
+    float p[4], q[4];
+    if (ok) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float xh, xl, yh, yl;
+        ok &= to_pair<BASE, K>(ux[e], xh, xl);
+        ok &= to_pair<BASE, K>(uy[e], yh, yl);
+        if constexpr (BASE == FLYTE_F64 && K > 4) {
+          pair_times_pair(xh, xl, yh, yl, p[e], q[e]);
+        } else {
+          p[e] = __fmul_rn(xh, yh);
+          q[e] = __fmaf_rn(xh, yh, -p[e]);
+        }
+      }
+    }
+    if (ok) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) dw_add(acc[e], p[e], q[e]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc64 = fma(bits_to_double<BASE, K>(ux[e]), bits_to_double<BASE, K>(uy[e]), acc64);
+    }
+  }
+  // the n % 4 trailing elements, binary64
+  const int64_t j = (ngrp << 2) + tid;
+  if (j < n) {
+    acc64 = fma(code_to_double<BASE, K>(load_code_bytes<K>(X + j * K)),
+                code_to_double<BASE, K>(load_code_bytes<K>(Y + j * K)), acc64);
+  }
+  double v = acc64;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) v += dw_value(acc[e]);
+  v = block_sum(v, smem);
+  if (threadIdx.x == 0) partial[blockIdx.x] = v;
+}
+
+// Any formats, strides and alignments: binary64 FMAs over the raw bytes.
+__global__ void __launch_bounds__(kThreads) dot_generic(const uint8_t* __restrict__ X, int kx, int bx, int64_t incx,
+                                                        const uint8_t* __restrict__ Y, int ky, int by, int64_t incy,
+                                                        int64_t n, double* __restrict__ partial) {
+  __shared__ double smem[kThreads / 32];
+  double acc = 0.0;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double a = code_to_double_rt(load_code_bytes_rt(X + i * incx * kx, kx), kx, bx);
+    const double b = code_to_double_rt(load_code_bytes_rt(Y + i * incy * ky, ky), ky, by);
+    acc = fma(a, b, acc);
+  }
+  acc = block_sum(acc, smem);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// Fixed-order sum of the per-block partials (pairwise over the block).
+__global__ void __launch_bounds__(kThreads) dot_finish(const double* __restrict__ partial, int nblocks,
+                                                       double* __restrict__ result) {
+  __shared__ double smem[kThreads / 32];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += kThreads) v += partial[b];
+  v = block_sum(v, smem);
+  if (threadIdx.x == 0) *result = v;
+}
+
+// ---- axpy -----------------------------------------------------------------------
+
+template <int BASE, int K>
+__device__ __forceinline__ uint64_t axpy_one(typename Native<BASE>::bits ux, typename Native<BASE>::bits uy,
+                                             double alpha, float alpha_f, int mode) {
+  if constexpr (BASE == FLYTE_F64) {
+    const double r = fma(alpha, __longlong_as_double((long long)ux), __longlong_as_double((long long)uy));
+    return narrow<BASE, K>(uint64_t(__double_as_longlong(r)), mode);
+  } else {
+    const float r = __fmaf_rn(alpha_f, __uint_as_float(ux), __uint_as_float(uy));
+    return narrow<BASE, K>(__float_as_uint(r), mode);
+  }
+}
+
+template <int BASE, int K>
+__global__ void __launch_bounds__(kThreads) axpy_groups(const uint8_t* __restrict__ X, uint8_t* __restrict__ Y,
+                                                        int64_t ngrp, double alpha, int mode) {
+  const float alpha_f = __double2float_rn(alpha);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngrp; g += stride) {
+    uint32_t wx[K], wy[K], wo[K];
+    load_group<K>(X + g * (4 * K), wx);
+    load_group_rw<K>(Y + g * (4 * K), wy);
+#pragma unroll
+    for (int j = 0; j < K; ++j) wo[j] = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      deposit_code<K>(wo, e, axpy_one<BASE, K>(extract_widened<BASE, K>(wx, e), extract_widened<BASE, K>(wy, e),
+                                               alpha, alpha_f, mode));
+    store_group<K>(Y + g * (4 * K), wo);
+  }
+}
+
+// Any widths of one base, strides and alignments: one element per thread.
+template <int BASE, int KY>
+__global__ void __launch_bounds__(kThreads) axpy_generic(const uint8_t* __restrict__ X, int kx, int64_t incx,
+                                                         uint8_t* __restrict__ Y, int64_t incy, int64_t first,
+                                                         int64_t n, double alpha, int mode) {
+  using Bits = typename Native<BASE>::bits;
+  constexpr int W = Native<BASE>::W;
+  const float alpha_f = __double2float_rn(alpha);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = first + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t qx = load_code_bytes_rt(X + i * incx * kx, kx);
+    const Bits ux = kx * 8 == W ? Bits(qx) : Bits(qx << (W - 8 * kx));
+    uint8_t* py = Y + i * incy * KY;
+    const Bits uy = widen<BASE, KY>(load_code_bytes<KY>(py));
+    store_code_bytes<KY>(py, axpy_one<BASE, KY>(ux, uy, alpha, alpha_f, mode));
+  }
+}
+
+bool aligned(const void* p, int bytes) { return reinterpret_cast<uintptr_t>(p) % bytes == 0; }
+
+int dot_blocks(int64_t work) {
+  int64_t b = (work + kThreads - 1) / kThreads;
+  if (b > kDotMaxBlocks) b = kDotMaxBlocks;
+  if (b < 1) b = 1;
+  return int(b);
+}
+
+}  // namespace
+
+size_t dot_workspace_bytes(int64_t n) {
+  (void)n;
+  return size_t(kHdrBytes + 8 * kDotMaxBlocks);
+}
+
+flyte_status launch_dot(double* result, int64_t n, const void* x, flyte_fmt fx, int64_t incx, const void* y,
+                        flyte_fmt fy, int64_t incy, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (ws == nullptr || ws_bytes < dot_workspace_bytes(n) || reinterpret_cast<uintptr_t>(ws) % 16 != 0) {
+    set_error("dot: workspace of %zu bytes (16-byte aligned) required", dot_workspace_bytes(n));
+    return FLYTE_ERR_WORKSPACE;
+  }
+  double* partial = reinterpret_cast<double*>(static_cast<uint8_t*>(ws) + kHdrBytes);
+  const uint8_t* X = static_cast<const uint8_t*>(x);
+  const uint8_t* Y = static_cast<const uint8_t*>(y);
+  const bool same = fx.k == fy.k && fx.base == fy.base;
+  const int S = group_bytes(fx.k);
+  const bool groups = same && incx == 1 && incy == 1 && aligned(x, S) && aligned(y, S) && n >= 4;
+  int nblocks;
+  if (groups) {
+    const int64_t ngrp = n / 4;
+    nblocks = dot_blocks(ngrp);
+    const int64_t L = (ngrp + int64_t(nblocks) * kThreads - 1) / (int64_t(nblocks) * kThreads);
+    const int fast = dw_bound_ok(n, L, 4 + 5 + 7 + (nblocks + kThreads - 1) / kThreads + 12, 20) ? 1 : 0;
+    flyte_status st = dispatch_fmt(fx, [&]<int BASE, int K>() -> flyte_status {
+      dot_groups<BASE, K><<<nblocks, kThreads, 0, s>>>(X, Y, ngrp, n, fast, partial);
+      FLYTE_TRY_LAUNCH("dot");
+      return FLYTE_OK;
+    });
+    if (st != FLYTE_OK) return st;
+  } else {
+    nblocks = dot_blocks(n);
+    dot_generic<<<nblocks, kThreads, 0, s>>>(X, fx.k, fx.base, incx, Y, fy.k, fy.base, incy, n, partial);
+    FLYTE_TRY_LAUNCH("dot");
+  }
+  dot_finish<<<1, kThreads, 0, s>>>(partial, nblocks, result);
+  FLYTE_TRY_LAUNCH("dot");
+  return FLYTE_OK;
+}
+
+flyte_status launch_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, int64_t incx, void* y,
+                         flyte_fmt fy, int64_t incy, int mode, cudaStream_t s) {
+  const uint8_t* X = static_cast<const uint8_t*>(x);
+  uint8_t* Y = static_cast<uint8_t*>(y);
+  return dispatch_fmt(fy, [&]<int BASE, int KY>() -> flyte_status {
+    int64_t first = 0;
+    const int S = group_bytes(KY);
+    if (fx.k == KY && incx == 1 && incy == 1 && aligned(x, S) && aligned(y, S) && n >= 4) {
+      const int64_t ngrp = n / 4;
+      axpy_groups<BASE, KY><<<grid_for(ngrp, kThreads), kThreads, 0, s>>>(X, Y, ngrp, alpha, mode);
+      FLYTE_TRY_LAUNCH("axpy");
+      first = ngrp * 4;
+    }
+    if (first < n) {
+      axpy_generic<BASE, KY><<<grid_for(n - first, kThreads), kThreads, 0, s>>>(X, fx.k, incx, Y, incy, first, n,
+                                                                               alpha, mode);
+      FLYTE_TRY_LAUNCH("axpy");
+    }
+    return FLYTE_OK;
+  });
+}
+
+}  // namespace flyte

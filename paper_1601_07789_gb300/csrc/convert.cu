@@ -21,49 +21,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kUnroll = 4;
 
-// Widest power-of-two access (<= 16 bytes) that divides a 4k-byte group.
-template <int K>
-__host__ __device__ constexpr int group_access_bytes() {
-  return (4 * K) % 16 == 0 ? 16 : ((4 * K) % 8 == 0 ? 8 : 4);
-}
-
-template <int K>
-__device__ __forceinline__ void load_group(const uint8_t* p, uint32_t (&w)[K]) {
-  constexpr int S = group_access_bytes<K>();
-  if constexpr (S == 16) {
-#pragma unroll
-    for (int i = 0; i < K / 4; ++i) {
-      uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + i);
-      w[4 * i] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
-    }
-  } else if constexpr (S == 8) {
-#pragma unroll
-    for (int i = 0; i < K / 2; ++i) {
-      uint2 v = __ldg(reinterpret_cast<const uint2*>(p) + i);
-      w[2 * i] = v.x; w[2 * i + 1] = v.y;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < K; ++i) w[i] = __ldg(reinterpret_cast<const uint32_t*>(p) + i);
-  }
-}
-
-template <int K>
-__device__ __forceinline__ void store_group(uint8_t* p, const uint32_t (&w)[K]) {
-  constexpr int S = group_access_bytes<K>();
-  if constexpr (S == 16) {
-#pragma unroll
-    for (int i = 0; i < K / 4; ++i)
-      reinterpret_cast<uint4*>(p)[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
-  } else if constexpr (S == 8) {
-#pragma unroll
-    for (int i = 0; i < K / 2; ++i) reinterpret_cast<uint2*>(p)[i] = make_uint2(w[2 * i], w[2 * i + 1]);
-  } else {
-#pragma unroll
-    for (int i = 0; i < K; ++i) reinterpret_cast<uint32_t*>(p)[i] = w[i];
-  }
-}
-
 // 4 native values: 16 bytes (float) or 32 bytes (double).
 template <int BASE>
 struct Quad {
@@ -199,7 +156,7 @@ flyte_status launch_unpack(void* dst, const void* src, int64_t n, flyte_fmt f, i
   return dispatch_fmt(f, [&]<int BASE, int K>() -> flyte_status {
     using Bits = typename Native<BASE>::bits;
     int64_t first = 0;
-    const bool fast = inc_src == 1 && inc_dst == 1 && aligned(src, group_access_bytes<K>()) && aligned(dst, 16);
+    const bool fast = inc_src == 1 && inc_dst == 1 && aligned(src, group_bytes(K)) && aligned(dst, 16);
     if (fast && n >= 4) {
       const int64_t ngroups = n / 4;
       unpack_groups<BASE, K><<<grid_for(ngroups, kThreads * kUnroll), kThreads, 0, s>>>(
@@ -221,7 +178,7 @@ flyte_status launch_pack(void* dst, const void* src, int64_t n, flyte_fmt f, int
                          int64_t inc_src, int mode, cudaStream_t s) {
   return dispatch_fmt(f, [&]<int BASE, int K>() -> flyte_status {
     int64_t first = 0;
-    const bool fast = inc_src == 1 && inc_dst == 1 && aligned(src, 16) && aligned(dst, group_access_bytes<K>());
+    const bool fast = inc_src == 1 && inc_dst == 1 && aligned(src, 16) && aligned(dst, group_bytes(K));
     if (fast && n >= 4) {
       const int64_t ngroups = n / 4;
       pack_groups<BASE, K><<<grid_for(ngroups, kThreads * kUnroll), kThreads, 0, s>>>(

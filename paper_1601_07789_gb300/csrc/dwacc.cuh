@@ -1,0 +1,164 @@
+// dwacc.cuh -- binary64-accurate dot products on the binary32 pipe.
+//
+// GB300 executes binary64 FMAs at 1/64 of the binary32 rate, too slow to keep
+// up with a k-byte stream from HBM.  The BLAS kernels therefore widen each
+// flyte to binary32 instead of binary64 (exactly: a double-based flyte with
+// k <= 4 has at most 21 significant bits; k >= 5 is split into an exact
+// high/low pair) whenever its exponent lies in a safe window, and accumulate
+// in double-word ("float-float") arithmetic built from error-free
+// transformations:
+//
+//   p + e       = a * x1          (TwoProd with an FMA; exact)
+//   e'          = RN(a * x2 + e)  (low part of a*x, x = x1 + x2 + O(u^2 x))
+//   s + t       = S + p           (TwoSum; exact)
+//   v           = RN(RN(C + t) + e')
+//   (S, C)      = Fast2Sum(s, v)  (exact: |C| <= u|S| and |v| <= 5u max(|S|,|p|)
+//                                  make s a multiple of ulp(v) whenever |s| < |v|)
+//
+// With u = 2^-24, one step adds at most 6 u^2 P to the error, P the running
+// sum of |a x| of that accumulator, and the product adds at most 14 u^2 |a x|
+// (3 u^2 for k <= 4).  A chain of L terms therefore errs by at most
+// (6L + 14) u^2 sum|a x|; the kernels keep L small by spreading a dot product
+// over many independent accumulators.  Combining the accumulators in binary64
+// adds at most R 2^-53 sum|a x|, R the depth of the reduction, and the
+// epilogue fma(alpha, t, beta y) 2 2^-53 (|alpha t| + |beta y|).  The host only
+// takes this path when
+//   (6L + 14) * 32 + R <= 4 n                 (u^2 = 32 * 2^-53)
+// so that the result meets |y - y_exact| <= 4 (n + 2) 2^-53 (|alpha| sum|a x| + |beta y|).
+// Elements outside the window (zero, subnormal, huge, Inf, NaN) are detected
+// with one integer compare each; the affected row, tile or group is then
+// summed with binary64 FMAs instead, which also gives IEEE Inf/NaN semantics.
+//
+// All binary32 operations use the _rn intrinsics so that the compiler cannot
+// contract them into FMAs and break the error-free transformations.
+#pragma once
+
+#include "flyte_internal.cuh"
+
+namespace flyte {
+
+struct DW {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void dw_zero(DW& a) { a.hi = 0.f; a.lo = 0.f; }
+
+// (S, C) <- (S, C) + (p + e) with the algorithm above.
+__device__ __forceinline__ void dw_add(DW& acc, float p, float e) {
+  const float s = __fadd_rn(acc.hi, p);
+  const float bp = __fsub_rn(s, acc.hi);
+  const float ap = __fsub_rn(s, bp);
+  const float t = __fadd_rn(__fsub_rn(acc.hi, ap), __fsub_rn(p, bp));
+  const float v = __fadd_rn(__fadd_rn(acc.lo, t), e);
+  const float hi = __fadd_rn(s, v);
+  acc.lo = __fsub_rn(v, __fsub_rn(hi, s));
+  acc.hi = hi;
+}
+
+// Exact binary64 value of a double-word accumulator (|lo| <= u |hi|).
+__device__ __forceinline__ double dw_value(const DW& a) { return double(a.hi) + double(a.lo); }
+
+// ---- exponent window ------------------------------------------------------
+//
+// A value is "in window" when 2^-40 <= |v| < 2^40.  Products of two in-window
+// values (or of one and a scaled x in [2^-40, 2)) stay within [2^-80, 2^81),
+// so every error term of the double-word algorithm is a normal binary32
+// number and no partial sum can overflow.
+
+constexpr int kWinLog2 = 40;
+
+// Double-based flyte element, widened to its 64-bit pattern (hi word h, low
+// word l), as binary32 pieces: value = hi + lo exactly for k <= 7 (lo = 0 for
+// k <= 4); for k = 8 lo keeps 23 of the 29 remaining bits (|error| < 2^-46 |v|).
+// Returns false when the value is outside the window (including zero).
+template <int K>
+__device__ __forceinline__ bool dbl_to_pair(uint32_t h, uint32_t l, float& hi, float& lo) {
+  constexpr uint32_t kElo = 1023 - kWinLog2;               // lowest exponent field in window
+  const uint32_t v = (h << 1) - (kElo << 21);
+  const bool ok = v < (uint32_t(2 * kWinLog2) << 21);
+  // binary32 pattern: sign | (e - 896) << 23 | top 23 mantissa bits (valid in window)
+  uint32_t mag;
+  if constexpr (K <= 4) {
+    mag = (h << 3) - (896u << 23);
+  } else {
+    mag = __funnelshift_l(l, h, 3) - (896u << 23);
+  }
+  const uint32_t hb = mag | (h & 0x80000000u);
+  hi = __uint_as_float(hb);
+  if constexpr (K <= 4) {
+    lo = 0.f;
+  } else {
+    // remaining bits l[28:0] weigh 2^(e - 1075); keep at most 23 of them
+    constexpr int kBits = 8 * (K - 4) - 3;                   // 5, 13, 21, 29
+    constexpr int kSh = kBits > 23 ? 29 - 23 : 29 - kBits;   // shift so they fit 23 bits
+    const uint32_t L = (l & 0x1FFFFFFFu) >> kSh;
+    const float lf = __fsub_rn(__uint_as_float(0x4B000000u | L), 8388608.0f);
+    // scale = sign * 2^(e - 1075 + kSh): exponent field of hi minus (52 - kSh)
+    const uint32_t sb = (hb & 0xFF800000u) - (uint32_t(52 - kSh) << 23);
+    lo = __fmul_rn(lf, __uint_as_float(sb));
+  }
+  return ok;
+}
+
+// Float-based flyte element widened to its binary32 pattern f.
+__device__ __forceinline__ bool flt_in_window(uint32_t f) {
+  constexpr uint32_t kElo = 127 - kWinLog2;
+  return ((f << 1) - (kElo << 24)) < (uint32_t(2 * kWinLog2) << 24);
+}
+
+// Product of an in-window element (hi + lo) with x = x1 + x2 as (p, e').
+__device__ __forceinline__ void pair_times_x(float ahi, float alo, float x1, float x2, float& p,
+                                             float& e) {
+  p = __fmul_rn(ahi, x1);
+  float t = __fmaf_rn(ahi, x1, -p);
+  t = __fmaf_rn(alo, x1, t);
+  e = __fmaf_rn(ahi, x2, t);
+}
+
+// Product of two in-window split elements (ahi + alo)(bhi + blo) as (p, e');
+// the alo*blo term (< 4u^2 |ab|) is dropped.
+__device__ __forceinline__ void pair_times_pair(float ahi, float alo, float bhi, float blo, float& p,
+                                                float& e) {
+  p = __fmul_rn(ahi, bhi);
+  float t = __fmaf_rn(ahi, bhi, -p);
+  t = __fmaf_rn(alo, bhi, t);
+  e = __fmaf_rn(ahi, blo, t);
+}
+
+__device__ __forceinline__ void single_times_x(float a, float x1, float x2, float& p, float& e) {
+  p = __fmul_rn(a, x1);
+  const float t = __fmaf_rn(a, x1, -p);
+  e = __fmaf_rn(a, x2, t);
+}
+
+// ---- warp / block reductions in binary64 (fixed order: deterministic) ----------
+
+// True when a length-n dot product summed in chains of at most L terms and
+// combined by a binary64 reduction of depth R meets the bound above.  P is
+// the product-error constant: 14 when one operand is binary64 x = x1 + x2,
+// 20 when both operands are flytes split into high/low pairs (flyte_dot).
+__host__ __device__ constexpr bool dw_bound_ok(int64_t n, int64_t L, int64_t R, int64_t P = 14) {
+  return (6 * L + P) * 32 + R <= 4 * n;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+// Sum over the block (blockDim.x / 32 warps) in a fixed order; result in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* smem) {
+  v = warp_sum(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += smem[w];
+  }
+  return t;
+}
+
+}  // namespace flyte

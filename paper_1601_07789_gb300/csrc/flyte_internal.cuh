@@ -178,6 +178,73 @@ __device__ __forceinline__ void deposit_code(uint32_t (&w)[NW], int e, uint64_t 
   }
 }
 
+// ---- 4-element groups: aligned vector access to 4k packed bytes ----------------------
+
+// Widest power-of-two access (<= 16 bytes) that divides a 4k-byte group; the
+// fast paths need the stream (and every row start) aligned to it.
+__host__ __device__ constexpr int group_bytes(int K) {
+  return (4 * K) % 16 == 0 ? 16 : ((4 * K) % 8 == 0 ? 8 : 4);
+}
+
+template <int K>
+__device__ __forceinline__ void load_group(const uint8_t* p, uint32_t (&w)[K]) {
+  constexpr int S = group_bytes(K);
+  if constexpr (S == 16) {
+#pragma unroll
+    for (int i = 0; i < K / 4; ++i) {
+      uint4 v = __ldg(reinterpret_cast<const uint4*>(p) + i);
+      w[4 * i] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
+    }
+  } else if constexpr (S == 8) {
+#pragma unroll
+    for (int i = 0; i < K / 2; ++i) {
+      uint2 v = __ldg(reinterpret_cast<const uint2*>(p) + i);
+      w[2 * i] = v.x; w[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < K; ++i) w[i] = __ldg(reinterpret_cast<const uint32_t*>(p) + i);
+  }
+}
+
+// Same, for a stream that the kernel also writes (no read-only cache path).
+template <int K>
+__device__ __forceinline__ void load_group_rw(const uint8_t* p, uint32_t (&w)[K]) {
+  constexpr int S = group_bytes(K);
+  if constexpr (S == 16) {
+#pragma unroll
+    for (int i = 0; i < K / 4; ++i) {
+      uint4 v = reinterpret_cast<const uint4*>(p)[i];
+      w[4 * i] = v.x; w[4 * i + 1] = v.y; w[4 * i + 2] = v.z; w[4 * i + 3] = v.w;
+    }
+  } else if constexpr (S == 8) {
+#pragma unroll
+    for (int i = 0; i < K / 2; ++i) {
+      uint2 v = reinterpret_cast<const uint2*>(p)[i];
+      w[2 * i] = v.x; w[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < K; ++i) w[i] = reinterpret_cast<const uint32_t*>(p)[i];
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void store_group(uint8_t* p, const uint32_t (&w)[K]) {
+  constexpr int S = group_bytes(K);
+  if constexpr (S == 16) {
+#pragma unroll
+    for (int i = 0; i < K / 4; ++i)
+      reinterpret_cast<uint4*>(p)[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+  } else if constexpr (S == 8) {
+#pragma unroll
+    for (int i = 0; i < K / 2; ++i) reinterpret_cast<uint2*>(p)[i] = make_uint2(w[2 * i], w[2 * i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < K; ++i) reinterpret_cast<uint32_t*>(p)[i] = w[i];
+  }
+}
+
 // ---- scalar byte access for the generic (any stride / alignment) paths ----------
 
 template <int K>
@@ -192,6 +259,30 @@ template <int K>
 __device__ __forceinline__ void store_code_bytes(uint8_t* p, uint64_t q) {
 #pragma unroll
   for (int b = 0; b < K; ++b) p[b] = uint8_t(q >> (8 * b));
+}
+
+// Exact binary64 value of a k-byte code.
+template <int BASE, int K>
+__device__ __forceinline__ double code_to_double(uint64_t q) {
+  if constexpr (BASE == FLYTE_F64) {
+    return __longlong_as_double((long long)widen<BASE, K>(q));
+  } else {
+    return double(__uint_as_float(widen<BASE, K>(q)));
+  }
+}
+
+// Runtime-format variants for the generic paths.
+__device__ __forceinline__ uint64_t load_code_bytes_rt(const uint8_t* p, int k) {
+  uint64_t q = 0;
+  for (int b = k - 1; b >= 0; --b) q = (q << 8) | uint64_t(p[b]);
+  return q;
+}
+
+__device__ __forceinline__ double code_to_double_rt(uint64_t q, int k, int base) {
+  if (base == FLYTE_F64) {
+    return __longlong_as_double((long long)(k == 8 ? q : (q << (64 - 8 * k))));
+  }
+  return double(__uint_as_float(uint32_t(k == 4 ? q : (q << (32 - 8 * k)))));
 }
 
 // ---- launch geometry -----------------------------------------------------------
@@ -243,5 +334,14 @@ flyte_status launch_pack(void* dst, const void* src, int64_t n, flyte_fmt f, int
                          int64_t inc_src, int mode, cudaStream_t s);
 flyte_status launch_unpack(void* dst, const void* src, int64_t n, flyte_fmt f, int64_t inc_dst,
                            int64_t inc_src, cudaStream_t s);
+flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const void* A, flyte_fmt fa,
+                         int64_t lda, const double* x, int64_t incx, double beta, double* y, int64_t incy,
+                         void* ws, size_t ws_bytes, cudaStream_t s);
+size_t gemv_workspace_bytes(char trans, int64_t m, int64_t n, flyte_fmt f);
+flyte_status launch_dot(double* result, int64_t n, const void* x, flyte_fmt fx, int64_t incx, const void* y,
+                        flyte_fmt fy, int64_t incy, void* ws, size_t ws_bytes, cudaStream_t s);
+size_t dot_workspace_bytes(int64_t n);
+flyte_status launch_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, int64_t incx, void* y,
+                         flyte_fmt fy, int64_t incy, int mode, cudaStream_t s);
 
 }  // namespace flyte
