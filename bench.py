@@ -1,0 +1,501 @@
+#!/usr/bin/env python3
+"""Benchmark of the flyte hot path on GB300 (prints one JSON line on rank 0).
+
+Workload (one step): y <- 1.5 op(A) x - 0.5 y on a 16384 x 16384 row-major
+matrix A with N(0,1) entries stored double-based at k = 3, 4, 5, 6 bytes per
+element, op = N and T for every k: eight flyte_gemv calls per step.  A, x and
+y are synthetic and seeded; A (0.75 to 1.5 GiB per k) is larger than the L2
+cache, so no flush is needed between steps.
+
+Reported:
+  value      effective GB/s of the whole step: algorithmic bytes (A k bytes per
+             element, x read, y read and written) / device time, summed over
+             ranks (replicas: every rank runs the same workload on its GPU)
+  per_k      per (k, op): time, GB/s, GFLOP/s and the speedup over native
+             binary64 gemv (cuBLAS DGEMV through torch.mv on the same GPU)
+  roofline   the kernel with the largest share of the step against the
+             measured HBM copy bandwidth
+  e2e        the same metric through the public API with the coded matrices,
+             x and y in pinned host memory, copied in and y copied back every step
+  rows       the other hot-path rows measured on their own (pack/unpack,
+             dot/axpy, gemm), each against its roofline
+  cpu_baseline  the CPU oracle on a bounded sample of the workload
+
+`--impl reference` times the CPU oracle itself as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+M = N = 16384
+KS = (3, 4, 5, 6)
+ALPHA, BETA = 1.5, -0.5
+WORKLOAD = "gemv y=1.5*op(A)x-0.5*y, A 16384x16384 N(0,1) double-based k in {3,4,5,6}, op in {N,T}"
+METRIC = "effective GB/s and GFLOP/s per byte width k; k-byte vs native FP64 gemv speedup"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["flyte", "reference"], default="flyte")
+    ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=6144, help="rows of the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def gemv_bytes(k: int, trans: str) -> int:
+    lenx, leny = (N, M) if trans == "N" else (M, N)
+    return M * N * k + 8 * lenx + 16 * leny
+
+
+def step_bytes() -> int:
+    return sum(gemv_bytes(k, t) for k in KS for t in "NT")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in ("paper_1601_07789_gb300/csrc/gemv.cu", "paper_1601_07789_gb300/csrc/dwacc.cuh",
+                "paper_1601_07789_gb300/csrc/flyte_internal.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t.get(kernel_key)
+        if e and e.get("source_hash") == source_hash():
+            return e["traffic_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", str(self.idx)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.monotonic(), parts))
+
+    def mark(self):
+        self.marks.append(time.monotonic())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        t0, t1 = (self.marks + [0, 0])[:2] if len(self.marks) >= 2 else (0, 1e30)
+        inside = [p for t, p in self.samples if t0 <= t <= t1]
+        use = inside if len(inside) >= 3 else [p for _, p in self.samples]
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for p in use if num(p[1]) is not None]
+        smax = [num(p[2]) for p in use if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in use for i in range(4) if p[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(use), "samples_in_timed_region": len(inside)}
+
+
+# ---- distributed plumbing -------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, local):
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        return dist
+    return None
+
+
+def max_over_ranks(dist, v: float) -> float:
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- CPU oracle sample ------------------------------------------------------------------
+
+def oracle_sample(rows: int, reps: int = 1):
+    """Time the oracle on `rows` x 16384 slices of the workload; returns (GB/s, seconds, desc)."""
+    import numpy as np
+
+    import oracle
+    from paper_1601_07789_gb300 import inputs
+    g = np.random.default_rng(2)
+    A = g.standard_normal((rows, N))
+    x = inputs.normal_f64(max(M, N), 3)
+    y = inputs.normal_f64(max(M, N), 4)
+    codes = {k: oracle.pack(A.reshape(-1), 1, k) for k in KS}
+    nbytes = 0
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for k in KS:
+            for trans in "NT":
+                if trans == "N":
+                    oracle.gemv("N", rows, N, ALPHA, codes[k], (1, k), N, x, 1, BETA, y, 1)
+                    nbytes += rows * N * k + 8 * N + 16 * rows
+                else:
+                    oracle.gemv("T", rows, N, ALPHA, codes[k], (1, k), N, x, 1, BETA, y, 1)
+                    nbytes += rows * N * k + 8 * rows + 16 * N
+    dt = time.perf_counter() - t0
+    desc = (f"{rows} of {M} rows of A (x full length) per (k, op), all eight gemv calls of a step, "
+            f"single-threaded C oracle")
+    return nbytes / dt / 1e9, dt, desc
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    rows = 256
+    for _ in range(args.warmup):
+        oracle_sample(rows)
+    total_t, total_gbs = 0.0, []
+    for _ in range(args.steps):
+        gbs, dt, desc = oracle_sample(rows)
+        total_t += dt
+        total_gbs.append(gbs)
+    value = statistics.mean(total_gbs)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded N(0,1))",
+        "config": {"workload": WORKLOAD, "sample_rows": rows, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---- GPU arm ------------------------------------------------------------------------------
+
+def run_flyte(args):
+    import torch
+
+    from paper_1601_07789_gb300 import flyte
+
+    rank, world, local = dist_env()
+    dist = init_dist(world, local)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    flyte.lib()
+    stream = torch.cuda.current_stream()
+
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2)
+    A64 = torch.randn(M * N, dtype=torch.float64, device=dev, generator=gen)
+    gen.manual_seed(3)
+    x = torch.randn(max(M, N), dtype=torch.float64, device=dev, generator=gen)
+    gen.manual_seed(4)
+    y = torch.randn(max(M, N), dtype=torch.float64, device=dev, generator=gen)
+    codes = {k: flyte.pack(A64, k) for k in KS}
+    ws = {t: torch.empty(flyte.workspace_bytes("gemv_n" if t == "N" else "gemv_t", M, N, 0, (6, 1)),
+                         dtype=torch.uint8, device=dev) for t in "NT"}
+
+    def call(k, trans, A=None, yv=None):
+        flyte.gemv(trans, M, N, ALPHA, codes[k] if A is None else A, (k, 1), N, x, BETA,
+                   y if yv is None else yv, ws=ws[trans])
+
+    calls = [(k, t) for k in KS for t in "NT"]
+    launches_per_step = sum(2 if t == "N" else 3 for _, t in calls)
+
+    for _ in range(args.warmup):
+        for k, t in calls:
+            call(k, t)
+    torch.cuda.synchronize()
+
+    ev = {c: [] for c in calls}
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.mark()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        for c in calls:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            call(*c)
+            b.record(stream)
+            ev[c].append((a, b))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark()
+    if dist:
+        dist.barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    elapsed_ms = max_over_ranks(dist, elapsed_ms)
+    sampler.stop()
+    clocks = sampler.summary()
+
+    per_call_ms = {c: statistics.mean(a.elapsed_time(b) for a, b in ev[c]) for c in calls}
+    value = world * args.steps * step_bytes() / (elapsed_ms * 1e-3) / 1e9
+
+    # native binary64 gemv on the same GPU (cuBLAS through torch) and our own k = 8
+    Am = A64.view(M, N)
+
+    def timeit(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(reps):
+            fn()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        return s0.elapsed_time(s1) / reps
+
+    yn = torch.empty(M, dtype=torch.float64, device=dev)
+    native_ms = {"N": timeit(lambda: torch.mv(Am, x[:N], out=yn)),
+                 "T": timeit(lambda: torch.mv(Am.t(), x[:M], out=yn))}
+    a8 = A64.view(torch.uint8)
+    k8_ms = {t: timeit(lambda t=t: flyte.gemv(t, M, N, ALPHA, a8, (8, 1), N, x, BETA, y, ws=ws[t]))
+             for t in "NT"}
+
+    per_k = {}
+    for k in KS:
+        per_k[f"k{k}"] = {}
+        for t in "NT":
+            ms = per_call_ms[(k, t)]
+            per_k[f"k{k}"][t] = {
+                "ms": round(ms, 4),
+                "GBps": round(gemv_bytes(k, t) / (ms * 1e-3) / 1e9, 1),
+                "GFLOPs": round(2 * M * N / (ms * 1e-3) / 1e9, 1),
+                "speedup_vs_native_fp64": round(native_ms[t] / ms, 3),
+            }
+    hbm_peak, peak_kind = load_peaks()
+    dom = max(calls, key=lambda c: per_call_ms[c])
+    dom_key = f"gemv_{dom[1].lower()}_kernel<F64,{dom[0]}>"
+    achieved = gemv_bytes(*dom) / (per_call_ms[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom_key, "achieved": round(achieved, 1), "peak": hbm_peak,
+                "peak_kind": f"of {peak_kind}", "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                "traffic": traffic_for(dom_key),
+                "note": "time of the whole flyte_gemv call (x preparation and, for T, the tile sum included)"}
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded N(0,1), generated on the device)",
+        "config": {"workload": WORKLOAD, "m": M, "n": N, "ks": list(KS), "ops": ["N", "T"],
+                   "step_bytes": step_bytes(), "l2": "inputs larger than L2 (A is 0.75-1.5 GiB per k)",
+                   "parallelism": f"replicas x{world}"},
+        "per_k": per_k,
+        "native_fp64": {"cublas_dgemv_ms": {t: round(v, 4) for t, v in native_ms.items()},
+                        "cublas_dgemv_GBps": {t: round(8 * M * N / (v * 1e-3) / 1e9, 1)
+                                              for t, v in native_ms.items()},
+                        "flyte_k8_ms": {t: round(v, 4) for t, v in k8_ms.items()}},
+        "roofline": roofline,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(args, codes, x, y, ws, dev, dist, world)
+    if not args.no_rows:
+        out["rows"] = run_rows(dev, hbm_peak)
+    del A64, codes
+    if rank == 0 and world == 1:
+        gbs, dt, desc = oracle_sample(args.cpu_rows)
+        out["cpu_baseline"] = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                               "sample": desc, "seconds": round(dt, 2)}
+    else:
+        out["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_e2e(args, codes, x, y, ws, dev, dist, world):
+    """Same metric through the public API from pinned host buffers, y read back every step."""
+    import torch
+
+    from paper_1601_07789_gb300 import flyte
+    host = {k: codes[k].cpu().pin_memory() for k in KS}
+    hx = x.cpu().pin_memory()
+    hy = y.cpu().pin_memory()
+    out_y = torch.empty_like(hy).pin_memory()
+    dA = {k: torch.empty_like(codes[k]) for k in KS}
+    dx = torch.empty_like(x)
+    dy = torch.empty_like(y)
+    steps = max(1, min(args.steps, 20))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for k in KS:
+            dA[k].copy_(host[k], non_blocking=True)
+        dx.copy_(hx, non_blocking=True)
+        dy.copy_(hy, non_blocking=True)
+        for k in KS:
+            for t in "NT":
+                flyte.gemv(t, M, N, ALPHA, dA[k], (k, 1), N, dx, BETA, dy, ws=ws[t])
+        out_y.copy_(dy, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(dist, e0.elapsed_time(e1))
+    h2d = sum(host[k].numel() for k in KS) + hx.numel() * 8 + hy.numel() * 8
+    return {"value": round(world * steps * step_bytes() / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": out_y.numel() * 8, "steps": steps,
+            "ms_per_step": round(ms / steps, 3)}
+
+
+def run_rows(dev, hbm_peak):
+    """Each other hot-path row timed on its own (CUDA events, averages over repetitions)."""
+    import torch
+
+    from paper_1601_07789_gb300 import flyte
+    stream = torch.cuda.current_stream()
+    rows = {}
+
+    def timeit(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(reps):
+            fn()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        return s0.elapsed_time(s1) / reps
+
+    def entry(nbytes, ms, flops=None):
+        d = {"ms": round(ms, 4), "GBps": round(nbytes / (ms * 1e-3) / 1e9, 1),
+             "frac_hbm": round(nbytes / (ms * 1e-3) / 1e9 / hbm_peak, 4)}
+        if flops:
+            d["GFLOPs"] = round(flops / (ms * 1e-3) / 1e9, 1)
+        return d
+
+    n = 1 << 28
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1601)
+    v = torch.randn(n, dtype=torch.float64, device=dev, generator=gen)
+    out = torch.empty_like(v)
+    for k in KS:
+        s = torch.empty(n * k, dtype=torch.uint8, device=dev)
+        rows[f"pack_f64_k{k}"] = entry(n * (8 + k), timeit(lambda: flyte.pack_raw(s, v, n, (k, 1))))
+        rows[f"unpack_f64_k{k}"] = entry(n * (8 + k), timeit(lambda: flyte.unpack_raw(out, s, n, (k, 1))))
+        del s
+    xs = flyte.pack(v, 4)
+    gen.manual_seed(1602)
+    ys = flyte.pack(torch.randn(n, dtype=torch.float64, device=dev, generator=gen), 4)
+    res = torch.empty((), dtype=torch.float64, device=dev)
+    wsd = torch.empty(flyte.workspace_bytes("dot", 0, n, 0, (4, 1)), dtype=torch.uint8, device=dev)
+    rows["dot_f64_k4"] = entry(2 * 4 * n, timeit(lambda: flyte.dot(xs, (4, 1), ys, (4, 1), n=n, out=res, ws=wsd)),
+                               2 * n)
+    rows["axpy_f64_k4"] = entry(3 * 4 * n, timeit(lambda: flyte.axpy(1e-9, xs, (4, 1), ys, (4, 1), n=n)), 2 * n)
+    rows["n"] = n
+    return rows
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_flyte(args)
+
+
+if __name__ == "__main__":
+    main()
