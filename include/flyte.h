@@ -128,6 +128,25 @@ flyte_status flyte_gemv(char trans, int64_t m, int64_t n, double alpha, const vo
                         int64_t lda, const double* x, int64_t incx, double beta, double* y,
                         int64_t incy, void* ws, size_t ws_bytes, cudaStream_t stream);
 
+/* gemv without a workspace argument.  The paper has no counterpart: this is
+ * for callers that cannot allocate device memory themselves (a plug-in inside
+ * a framework that owns all device allocations, or a serving loop that must
+ * not call cudaMalloc after start-up).  Same operation, arguments, accuracy
+ * and errors as flyte_gemv, with the scratch taken from a 4 MiB array built
+ * into the library (held by every GPU that loads it until exit):
+ *  - a call needing more than 4 MiB (flyte_workspace_bytes("gemv_n" or
+ *    "gemv_t", m, n, 0, fa)) returns FLYTE_ERR_WORKSPACE, launching nothing;
+ *  - the first call on each device looks up the array's address
+ *    (cudaGetSymbolAddress) with that device current: make it before any
+ *    stream capture;
+ *  - all calls share the array; nothing in it needs to start at zero, but
+ *    calls whose kernels overlap on the GPU (different streams or threads)
+ *    race on it.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+flyte_status flyte_gemv_static(char trans, int64_t m, int64_t n, double alpha, const void* A,
+                               flyte_fmt fa, int64_t lda, const double* x, int64_t incx, double beta,
+                               double* y, int64_t incy, cudaStream_t stream);
+
 /* ---- BLAS level 3 (Sec. 6.3.3) ----------------------------------------------- */
 
 /* gemm, row-major: C <- alpha * A B + beta * C with A m x k_ (lda >= k_),

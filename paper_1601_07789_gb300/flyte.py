@@ -26,8 +26,8 @@ STATUS = {0: "FLYTE_OK", 1: "FLYTE_ERR_INVALID_ARG", 2: "FLYTE_ERR_UNSUPPORTED",
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libflyte.so")
 
 # every entry point declared in include/flyte.h
-EXPORTS = ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_gemv", "flyte_gemm",
-           "flyte_workspace_bytes", "flyte_last_error_string", "flyte_version")
+EXPORTS = ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_gemv", "flyte_gemv_static",
+           "flyte_gemm", "flyte_workspace_bytes", "flyte_last_error_string", "flyte_version")
 
 
 class FlyteError(RuntimeError):
@@ -71,10 +71,12 @@ def lib() -> ctypes.CDLL:
             L.flyte_axpy.argtypes = [i64, dbl, vp, Fmt, i64, vp, Fmt, i64, i32, vp]
             L.flyte_gemv.argtypes = [ctypes.c_char, i64, i64, dbl, vp, Fmt, i64, vp, i64, dbl, vp,
                                      i64, vp, sz, vp]
+            L.flyte_gemv_static.argtypes = [ctypes.c_char, i64, i64, dbl, vp, Fmt, i64, vp, i64, dbl,
+                                            vp, i64, vp]
             L.flyte_gemm.argtypes = [i64, i64, i64, dbl, vp, Fmt, i64, vp, Fmt, i64, dbl, vp, i64,
                                      vp, sz, vp]
             for name in ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_gemv",
-                         "flyte_gemm"):
+                         "flyte_gemv_static", "flyte_gemm"):
                 getattr(L, name).restype = i32
             L.flyte_workspace_bytes.argtypes = [ctypes.c_char_p, i64, i64, i64, Fmt]
             L.flyte_workspace_bytes.restype = sz
@@ -204,6 +206,13 @@ def gemv(trans: str, m: int, n: int, alpha: float, A: torch.Tensor, fa, lda: int
         ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device=A.device)
     gemv_raw(trans.upper(), m, n, alpha, A, fa, lda, x, incx, beta, y, incy, ws, ws.numel(), stream)
     return y
+
+
+def gemv_static_raw(trans: str, m: int, n: int, alpha: float, A, fa, lda: int, x, incx: int,
+                    beta: float, y, incy: int, stream=None):
+    """gemv with the library's built-in scratch (no workspace; see flyte_gemv_static)."""
+    _check(lib().flyte_gemv_static(trans.encode(), m, n, float(alpha), _ptr(A), fmt(fa), lda, _ptr(x),
+                                   incx, float(beta), _ptr(y), incy, _stream(stream)))
 
 
 def gemm_raw(m: int, n: int, k: int, alpha: float, A, fa, lda: int, B, fb, ldb: int, beta: float,
