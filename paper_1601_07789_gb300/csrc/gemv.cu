@@ -4,29 +4,32 @@
 // each element costs few instructions: A is streamed once with aligned
 // vector loads of whole 4-element groups (4k bytes), widened in registers
 // (Sec. 4.1) and folded into double-word accumulators on the binary32 pipe
-// (dwacc.cuh).  x is prepared once per call as x' = x 2^-sx = x1 + x2 (two
-// binary32 arrays in the workspace, sx chosen so that max |x'| is in [1, 2)).
+// (dwacc.cuh).  x is split once per call into x = x1 + x2 (two binary32
+// arrays in the workspace); an x value outside the window gets x1 = NaN, so
+// every double-word sum that uses it comes out NaN and is redone in binary64.
 //
-//   'N': a block of 8 warps owns R rows; its 256 threads stride over the
-//        row in 4-element groups, 4 accumulators per row and thread (chains
-//        of n/1024 terms); warp and block reductions in binary64.
+//   'N': a block of 8 warps owns 16 rows (2 per warp) and one chunk of at
+//        most 4096 columns; all warps walk the same columns, so x1/x2 are
+//        fetched into L1 once per block.  Each lane keeps 4 accumulators per
+//        row (chains of chunk/128 terms); chunk sums go to the workspace and
+//        a second kernel adds them in a fixed order and applies the epilogue.
 //   'T': a block of 4 warps owns 512 columns and a tile of RB rows; each
-//        thread keeps 2 x 4 accumulators for its 4 columns; the per-tile
-//        column sums go to the workspace and a second kernel adds the tiles
-//        in a fixed order and applies the epilogue.
+//        thread keeps 2 x 4 accumulators for its 4 columns (rows alternate
+//        between them); the per-tile column sums go to the workspace and a
+//        second kernel adds the tiles in a fixed order.
 //
-// Whenever an element is outside the binary32 window, or x is, or the
-// pointers are not aligned for group loads, the affected row (N) or column
-// group (T) is recomputed with binary64 FMAs over the raw bytes.
+// Whenever an element is outside the binary32 window, or the pointers are
+// not aligned for group loads, the affected (row, chunk) of 'N' or (column
+// group, tile) of 'T' is recomputed with binary64 FMAs over the raw bytes.
+#include "bulkpipe.cuh"
 #include "dwacc.cuh"
 
 namespace flyte {
 namespace {
 
-constexpr int kHdrBytes = 256;
 
 // Fold element bits (widened native pattern) times x1 + x2 into acc.
-template <int BASE, int K>
+template <int BASE, int K, bool LAZY = false>
 __device__ __forceinline__ void fold(typename Native<BASE>::bits u, float x1, float x2, DW& acc, bool& ok) {
   float p, e;
   if constexpr (BASE == FLYTE_F64) {
@@ -41,195 +44,250 @@ __device__ __forceinline__ void fold(typename Native<BASE>::bits u, float x1, fl
     ok &= flt_in_window(u);
     single_times_x(__uint_as_float(u), x1, x2, p, e);
   }
-  dw_add(acc, p, e);
+  if constexpr (LAZY) {
+    dw_add_lazy(acc, p, e);
+  } else {
+    dw_add(acc, p, e);
+  }
 }
 
 __device__ __forceinline__ double epilogue(double t, double alpha, double beta, const double* yp) {
   return beta == 0.0 ? alpha * t : fma(alpha, t, beta * *yp);
 }
 
-// ---- x preparation: x' = x 2^-sx = x1 + x2 -------------------------------------
+// ---- x preparation: x = x1 + x2 --------------------------------------------------
 
-__global__ void __launch_bounds__(1024) prep_x(const double* __restrict__ x, int64_t len, int64_t incx,
-                                               int* __restrict__ hdr, float* __restrict__ x1,
-                                               float* __restrict__ x2) {
-  __shared__ int s_emax, s_bad;
-  if (threadIdx.x == 0) { s_emax = -1; s_bad = 0; }
-  __syncthreads();
-  int emax = -1, bad = 0;
-  for (int64_t j = threadIdx.x; j < len; j += blockDim.x) {
-    const uint64_t b = uint64_t(__double_as_longlong(x[j * incx]));
-    const int e = int((b >> 52) & 0x7FF);
-    if (e == 0x7FF) bad = 1;
-    else if ((b << 1) != 0) emax = max(emax, e);
-  }
-  emax = __reduce_max_sync(0xFFFFFFFFu, emax);
-  bad = __reduce_or_sync(0xFFFFFFFFu, bad);
-  if ((threadIdx.x & 31) == 0) { atomicMax(&s_emax, emax); atomicOr(&s_bad, bad); }
-  __syncthreads();
-  // scale so that the largest nonzero |x| lands in [1, 2)
-  const int sx = s_emax < 0 ? 0 : s_emax - 1023;
-  bad = s_bad || sx > 1000 || sx < -1000;
-  const double scale = __longlong_as_double((long long)(uint64_t(1023 - (bad ? 0 : sx)) << 52));
-  for (int64_t j = threadIdx.x; j < len; j += blockDim.x) {
-    const double v = x[j * incx] * scale;
-    const float a = __double2float_rn(v);
-    const float c = __double2float_rn(v - double(a));
-    if (v != 0.0 && fabs(v) < 0x1p-40) bad = 1;
+// x1 = RN32(x) and x2 = RN32(x - x1) (|x - x1 - x2| <= 2^-48 |x|) for x = 0 or
+// 2^-40 <= |x| < 2^40; any other x (tiny, huge, Inf, NaN) gets x1 = NaN.
+__global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int64_t len, int64_t incx,
+                                              float* __restrict__ x1, float* __restrict__ x2,
+                                              int* __restrict__ status) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *status = 0;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < len; j += stride) {
+    const double v = x[j * incx];
+    const double av = fabs(v);
+    const bool ok = v == 0.0 || (av >= 0x1p-40 && av < 0x1p40);
+    float a = __double2float_rn(v);
+    float c = __double2float_rn(v - double(a));
+    if (!ok) {
+      a = __uint_as_float(0x7FC00000u);
+      c = 0.f;
+    }
     x1[j] = a;
     x2[j] = c;
-  }
-  bad = __reduce_or_sync(0xFFFFFFFFu, bad);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0 && bad) atomicOr(&s_bad, 1);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    hdr[0] = sx;
-    hdr[1] = s_bad ? 0 : 1;
   }
 }
 
 // ---- gemv N ---------------------------------------------------------------------
 
-constexpr int kNThreads = 256;
+// Compile-time tuning knobs.  Defaults are the best of a sweep on GB300 at
+// 16384 x 16384 (unroll 2/4 and 4/8 rows per step, bulk pipeline on/off):
+// groups per step in 'N' is 2 for k <= 4 and 4 above; 'T' loads 4 rows per
+// step; the warp-private bulk pipeline is off (slower than direct loads).
+#ifndef FLYTE_N_UNROLL_SMALL_K
+#define FLYTE_N_UNROLL_SMALL_K 2
+#endif
+#ifndef FLYTE_N_UNROLL_LARGE_K
+#define FLYTE_N_UNROLL_LARGE_K 4
+#endif
+#ifndef FLYTE_T_ROWS
+#define FLYTE_T_ROWS 4
+#endif
+#ifndef FLYTE_GEMV_BULK
+#define FLYTE_GEMV_BULK 0
+#endif
 
-template <int BASE, int K, int R>
-__global__ void __launch_bounds__(kNThreads) gemv_n_kernel(
+constexpr int kNWarps = 8;
+constexpr int kNRowsPerWarp = 2;
+constexpr int kNRowsPerBlock = kNWarps * kNRowsPerWarp;
+constexpr int64_t kNChunkCols = 4096;   // columns per chunk, a multiple of 128
+template <int K>
+__host__ __device__ constexpr int n_unroll() { return K <= 4 ? FLYTE_N_UNROLL_SMALL_K : FLYTE_N_UNROLL_LARGE_K; }
+
+template <int BASE, int K, bool LAZY>
+__global__ void __launch_bounds__(kNWarps * 32) gemv_n_kernel(
     const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
-    const float* __restrict__ x2, const int* __restrict__ hdr, const double* __restrict__ x, int64_t incx,
-    double alpha, double beta, double* __restrict__ y, int64_t incy, int fast) {
-  using Bits = typename Native<BASE>::bits;
-  __shared__ double red[kNThreads / 32][R];
-  __shared__ double bsum[kNThreads / 32];
-  __shared__ int bad[R];
+    const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t chunk_cols,
+    int64_t nchunks, double* __restrict__ partial, double alpha, double beta, double* __restrict__ y,
+    int64_t incy, int fast) {
+  constexpr int kNUnroll = n_unroll<K>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t r0 = int64_t(blockIdx.x) * R;
-  const bool use_fast = fast && hdr[1] != 0;
-  if (threadIdx.x < R) bad[threadIdx.x] = use_fast ? 0 : 1;
-  __syncthreads();
-  if (use_fast) {
-    DW acc[R][4];
-    bool ok[R];
+  const int64_t row0 = int64_t(blockIdx.x) * kNRowsPerBlock + warp * kNRowsPerWarp;
+  if (row0 >= m) return;
+  const int64_t chunk = blockIdx.y;
+  const int64_t cb = chunk * chunk_cols;
+  const int64_t ce = min(n, cb + chunk_cols);
+  const int64_t gb = cb >> 2, ge = ce >> 2;           // whole groups of this chunk
+  const uint8_t* rowp[kNRowsPerWarp];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      ok[r] = true;
+  for (int r = 0; r < kNRowsPerWarp; ++r) rowp[r] = A + min(row0 + r, m - 1) * lda * K;
+
+  double v[kNRowsPerWarp];
+  bool ok[kNRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kNRowsPerWarp; ++r) { v[r] = 0.0; ok[r] = fast != 0; }
+  if (fast) {
+    DW acc[kNRowsPerWarp][4];
+#pragma unroll
+    for (int r = 0; r < kNRowsPerWarp; ++r)
 #pragma unroll
       for (int e = 0; e < 4; ++e) dw_zero(acc[r][e]);
+    int64_t g = gb + lane;
+    for (; g + 32 * (kNUnroll - 1) < ge; g += 32 * kNUnroll) {
+      float4 xa[kNUnroll], xb[kNUnroll];
+      uint32_t w[kNUnroll][kNRowsPerWarp][K];
+#pragma unroll
+      for (int u = 0; u < kNUnroll; ++u) {
+        const int64_t gu = g + 32 * u;
+        xa[u] = __ldg(reinterpret_cast<const float4*>(x1) + gu);
+        xb[u] = __ldg(reinterpret_cast<const float4*>(x2) + gu);
+#pragma unroll
+        for (int r = 0; r < kNRowsPerWarp; ++r) load_group<K>(rowp[r] + gu * (4 * K), w[u][r]);
+      }
+#pragma unroll
+      for (int u = 0; u < kNUnroll; ++u) {
+        const float xs1[4] = {xa[u].x, xa[u].y, xa[u].z, xa[u].w};
+        const float xs2[4] = {xb[u].x, xb[u].y, xb[u].z, xb[u].w};
+#pragma unroll
+        for (int r = 0; r < kNRowsPerWarp; ++r)
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            fold<BASE, K, LAZY>(extract_widened<BASE, K>(w[u][r], e), xs1[e], xs2[e], acc[r][e], ok[r]);
+      }
     }
-    const int64_t ngrp = n >> 2;
-    for (int64_t g = threadIdx.x; g < ngrp; g += kNThreads) {
+    for (; g < ge; g += 32) {
       const float4 xa = __ldg(reinterpret_cast<const float4*>(x1) + g);
       const float4 xb = __ldg(reinterpret_cast<const float4*>(x2) + g);
       const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
       const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
-      uint32_t w[R][K];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (r0 + r < m) load_group<K>(A + ((r0 + r) * lda + 4 * g) * K, w[r]);
-      }
+      for (int r = 0; r < kNRowsPerWarp; ++r) {
+        uint32_t w[K];
+        load_group<K>(rowp[r] + g * (4 * K), w);
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (r0 + r < m) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            fold<BASE, K>(extract_widened<BASE, K>(w[r], e), xs1[e], xs2[e], acc[r][e], ok[r]);
-        }
+        for (int e = 0; e < 4; ++e)
+          fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
       }
     }
-    const int64_t j = (ngrp << 2) + threadIdx.x;   // the n % 4 trailing elements
-    if (j < n) {
+    const int64_t j = (ge << 2) + lane;               // trailing n % 4 elements (last chunk only)
+    if (j < ce) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if (r0 + r < m) {
-          const uint64_t q = load_code_bytes<K>(A + ((r0 + r) * lda + j) * K);
-          fold<BASE, K>(widen<BASE, K>(q), x1[j], x2[j], acc[r][0], ok[r]);
-        }
+      for (int r = 0; r < kNRowsPerWarp; ++r) {
+        const uint64_t q = load_code_bytes<K>(rowp[r] + j * K);
+        fold<BASE, K, LAZY>(widen<BASE, K>(q), x1[j], x2[j], acc[r][0], ok[r]);
       }
     }
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const bool any_bad = __any_sync(0xFFFFFFFFu, !ok[r]);
-      double v = 0.0;
+    for (int r = 0; r < kNRowsPerWarp; ++r) {
+      double t = 0.0;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) v += dw_value(acc[r][e]);
-      v = warp_sum(v);
-      if (lane == 0) {
-        red[warp][r] = v;
-        if (any_bad) bad[r] = 1;
-      }
+      for (int e = 0; e < 4; ++e) t += dw_value(acc[r][e]);
+      t = warp_sum(t);
+      v[r] = t;
+      ok[r] = __all_sync(0xFFFFFFFFu, ok[r]) && isfinite(t);
     }
   }
-  __syncthreads();
-  const int sx = use_fast ? hdr[0] : 0;
-  for (int r = 0; r < R; ++r) {
-    const int64_t row = r0 + r;
+#pragma unroll
+  for (int r = 0; r < kNRowsPerWarp; ++r) {
+    const int64_t row = row0 + r;
     if (row >= m) break;
-    double t = 0.0;
-    if (bad[r]) {
-      // binary64 FMAs over the raw bytes of the row
+    if (!ok[r]) {
+      // binary64 FMAs over the raw bytes of this row and chunk
       const uint8_t* Ar = A + row * lda * K;
-      double v = 0.0;
-      for (int64_t c = threadIdx.x; c < n; c += kNThreads)
-        v = fma(code_to_double<BASE, K>(load_code_bytes<K>(Ar + c * K)), x[c * incx], v);
-      t = block_sum(v, bsum);
-    } else if (threadIdx.x == 0) {
-      for (int w = 0; w < kNThreads / 32; ++w) t += red[w][r];
-      t = ldexp(t, sx);
+      double s = 0.0;
+      for (int64_t c = cb + lane; c < ce; c += 32)
+        s = fma(code_to_double<BASE, K>(load_code_bytes<K>(Ar + c * K)), x[c * incx], s);
+      v[r] = warp_sum(s);
     }
-    if (threadIdx.x == 0) y[row * incy] = epilogue(t, alpha, beta, y + row * incy);
+    if (lane == 0) {
+      if (nchunks == 1) {
+        y[row * incy] = epilogue(v[r], alpha, beta, y + row * incy);
+      } else {
+        partial[row * nchunks + chunk] = v[r];
+      }
+    }
   }
-  (void)sizeof(Bits);
+}
+
+// Row sums over the chunks in chunk order, then the epilogue.
+__global__ void __launch_bounds__(256) gemv_n_finish(const double* __restrict__ partial, int64_t nchunks,
+                                                     int64_t m, double alpha, double beta,
+                                                     double* __restrict__ y, int64_t incy) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double t = 0.0;
+  for (int64_t c = 0; c < nchunks; ++c) t += partial[i * nchunks + c];
+  y[i * incy] = epilogue(t, alpha, beta, y + i * incy);
 }
 
 // ---- gemv T ---------------------------------------------------------------------
 
 constexpr int kTThreads = 128;
+constexpr int kTRowsPerIter = FLYTE_T_ROWS;   // rows loaded per iteration (a multiple of 4)
 
-template <int BASE, int K>
+template <int BASE, int K, bool LAZY>
 __global__ void __launch_bounds__(kTThreads) gemv_t_kernel(
     const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
-    const float* __restrict__ x2, const int* __restrict__ hdr, const double* __restrict__ x, int64_t incx,
-    int64_t rb, double* __restrict__ partial, int fast) {
+    const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t rb,
+    int64_t fold_rows, double* __restrict__ partial, int fast) {
+  constexpr int U = kTRowsPerIter;
   const int64_t cg = int64_t(blockIdx.x) * kTThreads + threadIdx.x;
   const int64_t c0 = cg * 4;
   if (c0 >= n) return;
   const int64_t i0 = int64_t(blockIdx.y) * rb;
   const int64_t i1 = min(m, i0 + rb);
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  bool ok = fast && hdr[1] != 0 && c0 + 4 <= n;
+  bool ok = fast && c0 + 4 <= n;
   if (ok) {
+    const uint8_t* colp = A + c0 * K;
     DW acc[2][4];
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int e = 0; e < 4; ++e) dw_zero(acc[h][e]);
-    constexpr int U = 4;
+    int64_t since = 0;
     int64_t i = i0;
     for (; i + U <= i1; i += U) {
       uint32_t w[U][K];
       float a1[U], a2[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        load_group<K>(A + ((i + u) * lda + c0) * K, w[u]);
-        a1[u] = __ldg(x1 + i + u);
-        a2[u] = __ldg(x2 + i + u);
+      for (int u = 0; u < U; u += 4) {
+        const float4 p = __ldg(reinterpret_cast<const float4*>(x1 + i + u));
+        const float4 q = __ldg(reinterpret_cast<const float4*>(x2 + i + u));
+        a1[u] = p.x; a1[u + 1] = p.y; a1[u + 2] = p.z; a1[u + 3] = p.w;
+        a2[u] = q.x; a2[u + 1] = q.y; a2[u + 2] = q.z; a2[u + 3] = q.w;
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) load_group<K>(colp + (i + u) * lda * K, w[u]);
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-          fold<BASE, K>(extract_widened<BASE, K>(w[u], e), a1[u], a2[u], acc[u & 1][e], ok);
+          fold<BASE, K, LAZY>(extract_widened<BASE, K>(w[u], e), a1[u], a2[u], acc[u & 1][e], ok);
+      since += U;
+      if (since >= fold_rows) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          v[e] += dw_value(acc[0][e]) + dw_value(acc[1][e]);
+          dw_zero(acc[0][e]);
+          dw_zero(acc[1][e]);
+        }
+        since = 0;
+      }
     }
     for (; i < i1; ++i) {
       uint32_t w[K];
-      load_group<K>(A + (i * lda + c0) * K, w);
-      const float a1 = __ldg(x1 + i), a2 = __ldg(x2 + i);
+      load_group<K>(colp + i * lda * K, w);
+      const float a1 = x1[i], a2 = x2[i];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) fold<BASE, K>(extract_widened<BASE, K>(w, e), a1, a2, acc[i & 1][e], ok);
+      for (int e = 0; e < 4; ++e) fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), a1, a2, acc[0][e], ok);
     }
-    const int sx = hdr[0];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = ldexp(dw_value(acc[0][e]) + dw_value(acc[1][e]), sx);
+    for (int e = 0; e < 4; ++e) {
+      v[e] += dw_value(acc[0][e]) + dw_value(acc[1][e]);
+      ok = ok && isfinite(v[e]);
+    }
   }
   if (!ok) {
     // binary64 FMAs over the raw bytes of this thread's columns
@@ -249,13 +307,311 @@ __global__ void __launch_bounds__(kTThreads) gemv_t_kernel(
     if (c0 + e < n) out[e] = v[e];
 }
 
-__global__ void gemv_t_finish(const double* __restrict__ partial, int64_t ntiles, int64_t n, double alpha,
-                              double beta, double* __restrict__ y, int64_t incy) {
-  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+// Column sums over the tiles: lane = column, warps take tiles w, w+8, ...;
+// the 8 warp sums are added in warp order, so the result is deterministic.
+__global__ void __launch_bounds__(256) gemv_t_finish(const double* __restrict__ partial, int64_t ntiles, int64_t n,
+                                                     double alpha, double beta, double* __restrict__ y,
+                                                     int64_t incy) {
+  __shared__ double red[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = int64_t(blockIdx.x) * 32 + lane;
   double t = 0.0;
-  for (int64_t s = 0; s < ntiles; ++s) t += partial[s * n + j];
-  y[j * incy] = epilogue(t, alpha, beta, y + j * incy);
+  if (j < n)
+    for (int64_t s = warp; s < ntiles; s += 8) t += partial[s * n + j];
+  red[warp][lane] = t;
+  __syncthreads();
+  if (warp == 0 && j < n) {
+    double sum = 0.0;
+    for (int w = 0; w < 8; ++w) sum += red[w][lane];
+    y[j * incy] = epilogue(sum, alpha, beta, y + j * incy);
+  }
+}
+
+// ---- bulk-pipelined variants ----------------------------------------------------------
+//
+// Same arithmetic as above, but each warp streams its operands through a
+// private ring of S shared-memory stages filled by cp.async.bulk (bulkpipe.cuh)
+// so that S - 1 stages per warp are in flight whatever the occupancy.  Needs
+// A and every row start 16-byte aligned; the launcher checks that.
+
+template <int K>
+__host__ __device__ constexpr int n_stage_bytes() { return 1024 + 2 * 128 * K; }          // x1, x2, two row segments
+template <int K>
+__host__ __device__ constexpr int n_stages() {
+  constexpr int s = 12288 / n_stage_bytes<K>();
+  return s < 3 ? 3 : (s > 8 ? 8 : s);
+}
+template <int K>
+__host__ __device__ constexpr int n_bulk_smem() { return kNWarps * n_stages<K>() * (n_stage_bytes<K>() + 8); }
+
+template <int BASE, int K, bool LAZY>
+__global__ void __launch_bounds__(kNWarps * 32) gemv_n_bulk(
+    const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
+    const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t chunk_cols,
+    int64_t nchunks, double* __restrict__ partial, double alpha, double beta, double* __restrict__ y,
+    int64_t incy, int* __restrict__ status) {
+  constexpr int S = n_stages<K>();
+  constexpr int kStage = n_stage_bytes<K>();
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* ring = smem + warp * S * kStage;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kNWarps * S * kStage) + warp * S;
+  const int64_t row0 = int64_t(blockIdx.x) * kNRowsPerBlock + warp * kNRowsPerWarp;
+  if (row0 >= m) return;
+  const int64_t chunk = blockIdx.y;
+  const int64_t cb = chunk * chunk_cols;
+  const int64_t ce = min(n, cb + chunk_cols);
+  const int64_t gb = cb >> 2, ge = ce >> 2;
+  const int64_t NI = (ge - gb) >> 5;                   // full 128-column steps, pipelined
+  const uint8_t* rowp[kNRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kNRowsPerWarp; ++r) rowp[r] = A + min(row0 + r, m - 1) * lda * K;
+
+  if (lane == 0) {
+    for (int i = 0; i < S; ++i) mbar_init(&bars[i], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  auto issue = [&](int64_t it) {
+    const int st = int(it % S);
+    uint8_t* d = ring + st * kStage;
+    const int64_t g0 = gb + 32 * it;
+    if (lane == 0) mbar_arrive_expect_tx(&bars[st], kStage);
+    __syncwarp();
+    if (lane < 4) {
+      fence_proxy_async_smem();
+      if (lane == 0) bulk_g2s(d, x1 + 4 * g0, 512, &bars[st]);
+      else if (lane == 1) bulk_g2s(d + 512, x2 + 4 * g0, 512, &bars[st]);
+      else bulk_g2s(d + 1024 + (lane - 2) * 128 * K, rowp[lane - 2] + 4 * g0 * K, 128 * K, &bars[st]);
+    }
+  };
+  const int64_t pro = NI < S ? NI : S;
+  for (int64_t it = 0; it < pro; ++it) issue(it);
+
+  DW acc[kNRowsPerWarp][4];
+  bool ok[kNRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kNRowsPerWarp; ++r) {
+    ok[r] = true;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dw_zero(acc[r][e]);
+  }
+  bool failed = false;
+  int64_t it = 0;
+  for (; it < NI; ++it) {
+    const int st = int(it % S);
+    const bool got = mbar_wait(&bars[st], uint32_t((it / S) & 1), status);
+    if (!__all_sync(0xFFFFFFFFu, got)) { failed = true; break; }
+    const uint8_t* d = ring + st * kStage;
+    const float4 xa = reinterpret_cast<const float4*>(d)[lane];
+    const float4 xb = reinterpret_cast<const float4*>(d + 512)[lane];
+    uint32_t w[kNRowsPerWarp][K];
+#pragma unroll
+    for (int r = 0; r < kNRowsPerWarp; ++r) lds_group<K>(d + 1024 + r * 128 * K + lane * 4 * K, w[r]);
+    __syncwarp();
+    if (it + S < NI) issue(it + S);
+    const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
+    const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+    for (int r = 0; r < kNRowsPerWarp; ++r)
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        fold<BASE, K, LAZY>(extract_widened<BASE, K>(w[r], e), xs1[e], xs2[e], acc[r][e], ok[r]);
+  }
+  if (failed) {
+    // drain the copies still in flight, then give up (the status word says why)
+    for (int64_t j = it; j < NI && j < it + S; ++j) mbar_wait(&bars[j % S], uint32_t((j / S) & 1), nullptr);
+    return;
+  }
+  // groups past the last full step, and the trailing n % 4 elements: direct loads
+  for (int64_t g = gb + 32 * NI + lane; g < ge; g += 32) {
+    const float4 xa = __ldg(reinterpret_cast<const float4*>(x1) + g);
+    const float4 xb = __ldg(reinterpret_cast<const float4*>(x2) + g);
+    const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
+    const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+    for (int r = 0; r < kNRowsPerWarp; ++r) {
+      uint32_t w[K];
+      load_group<K>(rowp[r] + g * (4 * K), w);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
+    }
+  }
+  const int64_t j = (ge << 2) + lane;
+  if (j < ce) {
+#pragma unroll
+    for (int r = 0; r < kNRowsPerWarp; ++r) {
+      const uint64_t q = load_code_bytes<K>(rowp[r] + j * K);
+      fold<BASE, K, LAZY>(widen<BASE, K>(q), x1[j], x2[j], acc[r][0], ok[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kNRowsPerWarp; ++r) {
+    double t = 0.0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) t += dw_value(acc[r][e]);
+    t = warp_sum(t);
+    const bool good = __all_sync(0xFFFFFFFFu, ok[r]) && isfinite(t);
+    const int64_t row = row0 + r;
+    if (row >= m) break;
+    if (!good) {
+      const uint8_t* Ar = A + row * lda * K;
+      double s2 = 0.0;
+      for (int64_t c = cb + lane; c < ce; c += 32)
+        s2 = fma(code_to_double<BASE, K>(load_code_bytes<K>(Ar + c * K)), x[c * incx], s2);
+      t = warp_sum(s2);
+    }
+    if (lane == 0) {
+      if (nchunks == 1) {
+        y[row * incy] = epilogue(t, alpha, beta, y + row * incy);
+      } else {
+        partial[row * nchunks + chunk] = t;
+      }
+    }
+  }
+}
+
+template <int K>
+__host__ __device__ constexpr int t_stage_bytes() { return 64 + kTRowsPerIter * 128 * K; }   // x1[8], x2[8], 8 row segments
+template <int K>
+__host__ __device__ constexpr int t_stages() {
+  constexpr int s = 16384 / t_stage_bytes<K>();
+  return s < 3 ? 3 : (s > 6 ? 6 : s);
+}
+template <int K>
+__host__ __device__ constexpr int t_bulk_smem() { return (kTThreads / 32) * t_stages<K>() * (t_stage_bytes<K>() + 8); }
+
+template <int BASE, int K, bool LAZY>
+__global__ void __launch_bounds__(kTThreads) gemv_t_bulk(
+    const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
+    const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t rb,
+    int64_t fold_rows, double* __restrict__ partial, int* __restrict__ status) {
+  constexpr int U = kTRowsPerIter;
+  constexpr int S = t_stages<K>();
+  constexpr int kStage = t_stage_bytes<K>();
+  constexpr int kWarps = kTThreads / 32;
+  extern __shared__ __align__(128) uint8_t smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* ring = smem + warp * S * kStage;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kWarps * S * kStage) + warp * S;
+  const int64_t c0w = (int64_t(blockIdx.x) * kWarps + warp) * 128;
+  if (c0w >= n) return;
+  const int64_t c0 = c0w + 4 * lane;
+  const int64_t i0 = int64_t(blockIdx.y) * rb;
+  const int64_t i1 = min(m, i0 + rb);
+  const bool whole = c0w + 128 <= n;                   // the warp's 128 columns all exist
+  const int64_t NI = whole ? (i1 - i0) / U : 0;
+  const uint8_t* colw = A + c0w * K;
+
+  if (lane == 0) {
+    for (int i = 0; i < S; ++i) mbar_init(&bars[i], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  auto issue = [&](int64_t it) {
+    const int st = int(it % S);
+    uint8_t* d = ring + st * kStage;
+    const int64_t r0 = i0 + U * it;
+    if (lane == 0) mbar_arrive_expect_tx(&bars[st], kStage);
+    __syncwarp();
+    if (lane < U + 2) {
+      fence_proxy_async_smem();
+      if (lane == 0) bulk_g2s(d, x1 + r0, 32, &bars[st]);
+      else if (lane == 1) bulk_g2s(d + 32, x2 + r0, 32, &bars[st]);
+      else bulk_g2s(d + 64 + (lane - 2) * 128 * K, colw + (r0 + lane - 2) * lda * K, 128 * K, &bars[st]);
+    }
+  };
+  const int64_t pro = NI < S ? NI : S;
+  for (int64_t it = 0; it < pro; ++it) issue(it);
+
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  bool ok = c0 + 4 <= n;
+  DW acc[2][4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dw_zero(acc[h][e]);
+  int64_t since = 0;
+  bool failed = false;
+  int64_t it = 0;
+  for (; it < NI; ++it) {
+    const int st = int(it % S);
+    const bool got = mbar_wait(&bars[st], uint32_t((it / S) & 1), status);
+    if (!__all_sync(0xFFFFFFFFu, got)) { failed = true; break; }
+    const uint8_t* d = ring + st * kStage;
+    float a1[U], a2[U];
+#pragma unroll
+    for (int u = 0; u < U; u += 4) {
+      const float4 p = reinterpret_cast<const float4*>(d)[u / 4];
+      const float4 q = reinterpret_cast<const float4*>(d + 32)[u / 4];
+      a1[u] = p.x; a1[u + 1] = p.y; a1[u + 2] = p.z; a1[u + 3] = p.w;
+      a2[u] = q.x; a2[u + 1] = q.y; a2[u + 2] = q.z; a2[u + 3] = q.w;
+    }
+    uint32_t w[U][K];
+#pragma unroll
+    for (int u = 0; u < U; ++u) lds_group<K>(d + 64 + u * 128 * K + lane * 4 * K, w[u]);
+    __syncwarp();
+    if (it + S < NI) issue(it + S);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        fold<BASE, K, LAZY>(extract_widened<BASE, K>(w[u], e), a1[u], a2[u], acc[u & 1][e], ok);
+    since += U;
+    if (since >= fold_rows) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        v[e] += dw_value(acc[0][e]) + dw_value(acc[1][e]);
+        dw_zero(acc[0][e]);
+        dw_zero(acc[1][e]);
+      }
+      since = 0;
+    }
+  }
+  if (failed) {
+    for (int64_t j = it; j < NI && j < it + S; ++j) mbar_wait(&bars[j % S], uint32_t((j / S) & 1), nullptr);
+    return;
+  }
+  if (ok) {
+    // rows past the last full step (and every row of a partial warp): direct loads
+    for (int64_t i = i0 + U * NI; i < i1; ++i) {
+      uint32_t w[K];
+      load_group<K>(A + (i * lda + c0) * K, w);
+      const float a1 = x1[i], a2 = x2[i];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), a1, a2, acc[i & 1][e], ok);
+      if (++since >= fold_rows) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          v[e] += dw_value(acc[0][e]) + dw_value(acc[1][e]);
+          dw_zero(acc[0][e]);
+          dw_zero(acc[1][e]);
+        }
+        since = 0;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      v[e] += dw_value(acc[0][e]) + dw_value(acc[1][e]);
+      ok = ok && isfinite(v[e]);
+    }
+  }
+  if (!ok) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      double s2 = 0.0;
+      if (c0 + e < n) {
+        for (int64_t i = i0; i < i1; ++i)
+          s2 = fma(code_to_double<BASE, K>(load_code_bytes<K>(A + (i * lda + c0 + e) * K)), x[i * incx], s2);
+      }
+      v[e] = s2;
+    }
+  }
+  double* out = partial + int64_t(blockIdx.y) * n + c0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    if (c0 + e < n) out[e] = v[e];
 }
 
 __global__ void scale_y(double* __restrict__ y, int64_t len, int64_t incy, double beta) {
@@ -264,45 +620,74 @@ __global__ void scale_y(double* __restrict__ y, int64_t len, int64_t incy, doubl
     y[j * incy] = beta == 0.0 ? 0.0 : beta * y[j * incy];
 }
 
-constexpr int kNRows = 4;          // rows per block in gemv N
-constexpr int64_t kTMaxRB = 256;   // row tile of gemv T
+constexpr int64_t kTRowTile = 128;   // row tile of gemv T
 
 int64_t align16(int64_t b) { return (b + 15) & ~int64_t(15); }
 
+// Opt a kernel into more than 48 KiB of dynamic shared memory (the attribute
+// is per function and device; setting it again is cheap and idempotent).
+template <typename Kern>
+bool set_smem_once(Kern kern, int bytes) {
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+}
+
 struct Plan {
-  bool fast;
-  int64_t rb, ntiles;
-  int64_t off_x1, off_x2, off_part, bytes;
+  bool fast, lazy;
+  int64_t chunk_cols, nchunks;        // N
+  int64_t rb, ntiles, fold_rows;      // T
+  int64_t off_status, off_x1, off_x2, off_part, bytes;
 };
 
-Plan plan_gemv(char trans, int64_t m, int64_t n, flyte_fmt f) {
+Plan plan_gemv(char trans, int64_t m, int64_t n) {
   Plan p{};
   const int64_t lenx = trans == 'N' ? n : m;
-  p.off_x1 = kHdrBytes;
+  p.off_status = 0;                   // int: error bits of the bulk pipelines
+  p.off_x1 = 16;
   p.off_x2 = p.off_x1 + align16(4 * lenx);
   p.off_part = p.off_x2 + align16(4 * lenx);
-  p.bytes = p.off_part;
   if (trans == 'N') {
-    const int64_t L = (n / 4 + kNThreads - 1) / kNThreads + 1;
-    p.fast = dw_bound_ok(n, L, 16);
-    p.rb = 0;
-    p.ntiles = 0;
+    // chunks of at most kNChunkCols columns (whole 128-column warp steps)
+    p.nchunks = (n + kNChunkCols - 1) / kNChunkCols;
+    p.chunk_cols = (((n + p.nchunks - 1) / p.nchunks) + 127) / 128 * 128;
+    p.nchunks = (n + p.chunk_cols - 1) / p.chunk_cols;
+    // chain: one term per 128-column step (+ one trailing element); reduction:
+    // 4 slots, 5 warp levels and the chunks
+    const int64_t L = p.chunk_cols / 128 + 1;
+    const int64_t R = 3 + 5 + p.nchunks + 1;
+    p.lazy = dw_lazy_bound_ok(n, L, R);
+    p.fast = p.lazy || dw_bound_ok(n, L, R);
+    p.bytes = p.off_part + (p.nchunks > 1 ? 8 * m * p.nchunks : 0);
   } else {
-    int64_t rb = kTMaxRB;
-    while (rb >= 16 && !dw_bound_ok(m, rb / 2, (m + rb - 1) / rb + 2)) rb /= 2;
-    p.fast = rb >= 16;
-    p.rb = p.fast ? rb : kTMaxRB;
+    p.rb = kTRowTile;
     p.ntiles = (m + p.rb - 1) / p.rb;
+    // chain: fold_rows / 2 rows per parity (+ up to kTRowsPerIter trailing
+    // rows); reduction: parities, folds of a tile and the tiles
+    const int64_t R = 2 + p.rb / kTRowsPerIter + p.ntiles + 2;
+    p.lazy = false;
+    p.fast = false;
+    p.fold_rows = p.rb;
+    for (int64_t f = 64; f >= kTRowsPerIter && !p.fast; f /= 2) {
+      if (dw_lazy_bound_ok(m, f / 2 + kTRowsPerIter, R)) {
+        p.fast = p.lazy = true;
+        p.fold_rows = f;
+      }
+    }
+    for (int64_t f = p.rb; f >= kTRowsPerIter && !p.fast; f /= 2) {
+      if (dw_bound_ok(m, f / 2 + kTRowsPerIter, R)) {
+        p.fast = true;
+        p.fold_rows = f;
+      }
+    }
     p.bytes = p.off_part + 8 * p.ntiles * n;
   }
-  (void)f;
   return p;
 }
 
 }  // namespace
 
 size_t gemv_workspace_bytes(char trans, int64_t m, int64_t n, flyte_fmt f) {
-  return size_t(plan_gemv(trans, m, n, f).bytes);
+  (void)f;
+  return size_t(plan_gemv(trans, m, n).bytes);
 }
 
 flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const void* A, flyte_fmt fa,
@@ -315,7 +700,7 @@ flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const v
     FLYTE_TRY_LAUNCH("gemv");
     return FLYTE_OK;
   }
-  const Plan p = plan_gemv(trans, m, n, fa);
+  const Plan p = plan_gemv(trans, m, n);
   if (ws == nullptr || ws_bytes < size_t(p.bytes)) {
     set_error("gemv: workspace of %lld bytes required", (long long)p.bytes);
     return FLYTE_ERR_WORKSPACE;
@@ -325,30 +710,70 @@ flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const v
     return FLYTE_ERR_WORKSPACE;
   }
   uint8_t* w8 = static_cast<uint8_t*>(ws);
-  int* hdr = reinterpret_cast<int*>(w8);
+  int* status = reinterpret_cast<int*>(w8 + p.off_status);
   float* x1 = reinterpret_cast<float*>(w8 + p.off_x1);
   float* x2 = reinterpret_cast<float*>(w8 + p.off_x2);
+  double* part = reinterpret_cast<double*>(w8 + p.off_part);
   const int64_t lenx = trans == 'N' ? n : m;
   return dispatch_fmt(fa, [&]<int BASE, int K>() -> flyte_status {
     constexpr int S = group_bytes(K);
     const bool aligned = reinterpret_cast<uintptr_t>(A) % S == 0 && (lda * K) % S == 0;
     const int fast = (p.fast && aligned) ? 1 : 0;
     if (fast) {
-      prep_x<<<1, 1024, 0, s>>>(x, lenx, incx, hdr, x1, x2);
+      prep_x<<<grid_for(lenx, 256), 256, 0, s>>>(x, lenx, incx, x1, x2, status);
       FLYTE_TRY_LAUNCH("gemv");
     }
     const uint8_t* A8 = static_cast<const uint8_t*>(A);
+    // bulk copies need A and every row start 16-byte aligned
+    const bool bulk = FLYTE_GEMV_BULK && fast && reinterpret_cast<uintptr_t>(A) % 16 == 0 && (lda * K) % 16 == 0;
     if (trans == 'N') {
-      const unsigned blocks = unsigned((m + kNRows - 1) / kNRows);
-      gemv_n_kernel<BASE, K, kNRows><<<blocks, kNThreads, 0, s>>>(A8, lda, m, n, x1, x2, hdr, x, incx, alpha,
-                                                                 beta, y, incy, fast);
+      dim3 grid(unsigned((m + kNRowsPerBlock - 1) / kNRowsPerBlock), unsigned(p.nchunks));
+      if (bulk) {
+        constexpr int smem = n_bulk_smem<K>();
+        if (p.lazy) {
+          if (!set_smem_once(gemv_n_bulk<BASE, K, true>, smem)) return cuda_status(cudaGetLastError(), "gemv");
+          gemv_n_bulk<BASE, K, true><<<grid, kNWarps * 32, smem, s>>>(A8, lda, m, n, x1, x2, x, incx, p.chunk_cols,
+                                                                      p.nchunks, part, alpha, beta, y, incy, status);
+        } else {
+          if (!set_smem_once(gemv_n_bulk<BASE, K, false>, smem)) return cuda_status(cudaGetLastError(), "gemv");
+          gemv_n_bulk<BASE, K, false><<<grid, kNWarps * 32, smem, s>>>(A8, lda, m, n, x1, x2, x, incx,
+                                                                       p.chunk_cols, p.nchunks, part, alpha, beta, y,
+                                                                       incy, status);
+        }
+      } else if (p.lazy) {
+        gemv_n_kernel<BASE, K, true><<<grid, kNWarps * 32, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.chunk_cols,
+                                                                   p.nchunks, part, alpha, beta, y, incy, fast);
+      } else {
+        gemv_n_kernel<BASE, K, false><<<grid, kNWarps * 32, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.chunk_cols,
+                                                                    p.nchunks, part, alpha, beta, y, incy, fast);
+      }
       FLYTE_TRY_LAUNCH("gemv");
+      if (p.nchunks > 1) {
+        gemv_n_finish<<<unsigned((m + 255) / 256), 256, 0, s>>>(part, p.nchunks, m, alpha, beta, y, incy);
+        FLYTE_TRY_LAUNCH("gemv");
+      }
     } else {
-      double* part = reinterpret_cast<double*>(w8 + p.off_part);
       dim3 grid(unsigned((n + 4 * kTThreads - 1) / (4 * kTThreads)), unsigned(p.ntiles));
-      gemv_t_kernel<BASE, K><<<grid, kTThreads, 0, s>>>(A8, lda, m, n, x1, x2, hdr, x, incx, p.rb, part, fast);
+      if (bulk) {
+        constexpr int smem = t_bulk_smem<K>();
+        if (p.lazy) {
+          if (!set_smem_once(gemv_t_bulk<BASE, K, true>, smem)) return cuda_status(cudaGetLastError(), "gemv");
+          gemv_t_bulk<BASE, K, true><<<grid, kTThreads, smem, s>>>(A8, lda, m, n, x1, x2, x, incx, p.rb, p.fold_rows,
+                                                                   part, status);
+        } else {
+          if (!set_smem_once(gemv_t_bulk<BASE, K, false>, smem)) return cuda_status(cudaGetLastError(), "gemv");
+          gemv_t_bulk<BASE, K, false><<<grid, kTThreads, smem, s>>>(A8, lda, m, n, x1, x2, x, incx, p.rb,
+                                                                    p.fold_rows, part, status);
+        }
+      } else if (p.lazy) {
+        gemv_t_kernel<BASE, K, true><<<grid, kTThreads, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.rb, p.fold_rows,
+                                                                part, fast);
+      } else {
+        gemv_t_kernel<BASE, K, false><<<grid, kTThreads, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.rb,
+                                                                 p.fold_rows, part, fast);
+      }
       FLYTE_TRY_LAUNCH("gemv");
-      gemv_t_finish<<<unsigned((n + 255) / 256), 256, 0, s>>>(part, p.ntiles, n, alpha, beta, y, incy);
+      gemv_t_finish<<<unsigned((n + 31) / 32), 256, 0, s>>>(part, p.ntiles, n, alpha, beta, y, incy);
       FLYTE_TRY_LAUNCH("gemv");
     }
     return FLYTE_OK;

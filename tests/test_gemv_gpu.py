@@ -45,9 +45,13 @@ def run_gemv(trans, m, n, fa, Acodes, lda, x, y0, alpha, beta, incx=1, incy=1, a
     xd = _dev(x)
     yd = _dev(y0.copy())
     wsb = flyte.workspace_bytes("gemv_n" if trans == "N" else "gemv_t", m, n, 0, fa)
-    ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device="cuda")
+    ws = torch.full((max(wsb, 16),), 0x55, dtype=torch.uint8, device="cuda")
     flyte.gemv_raw(trans, m, n, alpha, A_ptr, fa, lda, xd, incx, beta, yd, incy, ws, ws.numel())
     sync()
+    if alpha != 0.0:
+        # the first word of the workspace is the pipelines' error word: no timeout happened
+        status = int(ws[:4].cpu().numpy().view(np.int32)[0])
+        assert status in (0, 0x55555555), f"pipeline status {status:#x}"
     return yd.cpu().numpy()
 
 
@@ -76,9 +80,10 @@ DFORMATS = [(k, 1) for k in range(1, 9)] + [(k, 0) for k in range(1, 5)]
 
 @pytest.mark.parametrize("fa", DFORMATS, ids=lambda f: f"k{f[0]}{'d' if f[1] else 'f'}")
 @pytest.mark.parametrize("trans", ["N", "T"])
-def test_gemv_parity_moderate(fa, trans):
-    m, n = 777, 1283
-    lda = n + 5
+@pytest.mark.parametrize("shape", [(777, 1283, 1288), (2100, 613, 618), (777, 1283, 1296),
+                                   (2100, 1024, 1024), (1500, 5000, 5008)])
+def test_gemv_parity_moderate(fa, trans, shape):
+    m, n, lda = shape
     A = make_A(m, lda, fa, seed=3 + fa[0])
     g = np.random.default_rng(17)
     x = g.standard_normal(max(m, n))
@@ -93,7 +98,9 @@ def test_gemv_parity_moderate(fa, trans):
 
 
 @pytest.mark.parametrize("trans", ["N", "T"])
-@pytest.mark.parametrize("shape", [(1, 1), (3, 7), (5, 300), (300, 5), (257, 1029), (64, 4099)])
+@pytest.mark.parametrize("shape", [(1, 1), (3, 7), (5, 300), (300, 5), (257, 1029), (64, 4099),
+                                   (1030, 64), (4099, 37), (2500, 2500), (2500, 2560), (3000, 9000),
+                                   (16, 12288)])
 def test_gemv_shapes_and_tails(trans, shape):
     m, n = shape
     fa = (5, 1)
@@ -112,7 +119,7 @@ def test_gemv_shapes_and_tails(trans, shape):
 @pytest.mark.parametrize("kind", ["positive", "wide"])
 def test_gemv_adversarial(trans, kind):
     """All-positive terms (errors cannot cancel) and a 2^+-60 spread of magnitudes."""
-    m, n = 600, 2051
+    m, n = 2600, 2051
     fa = (4, 1)
     A = make_A(m, n, fa, seed=5, kind=kind)
     x = np.abs(np.random.default_rng(6).standard_normal(max(m, n))) + 0.25
@@ -126,7 +133,7 @@ def test_gemv_adversarial(trans, kind):
 @pytest.mark.parametrize("trans", ["N", "T"])
 def test_gemv_specials_and_zeros(trans):
     """Zeros, subnormals, Inf and NaN in A, and Inf in x, take the binary64 path."""
-    m, n = 300, 1030
+    m, n = 2100, 1030
     fa = (6, 1)
     g = np.random.default_rng(8)
     v = g.standard_normal(m * n)
