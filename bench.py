@@ -486,7 +486,63 @@ def run_rows(dev, hbm_peak):
                                2 * n)
     rows["axpy_f64_k4"] = entry(3 * 4 * n, timeit(lambda: flyte.axpy(1e-9, xs, (4, 1), ys, (4, 1), n=n)), 2 * n)
     rows["n"] = n
+    del v, out, xs, ys
+    rows.update(run_gemm_rows(dev))
     return rows
+
+
+def run_gemm_rows(dev):
+    """gemm rows: float-based k = 2, 3, 4 at 8192^3 and double-based k = 5 at 4096^3, U(-1,1)."""
+    import torch
+
+    from paper_1601_07789_gb300 import flyte
+    stream = torch.cuda.current_stream()
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+    fp64_peak = 1.25   # nominal dense FP64 tensor rate of this GPU (TFLOP/s); no measured figure
+    out = {}
+
+    def timeit(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(reps):
+            fn()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        return s0.elapsed_time(s1) / reps
+
+    for k, size, reps in ((2, 8192, 5), (3, 8192, 3), (4, 8192, 3), (5, 4096, 2)):
+        base = 0 if k <= 4 else 1
+        f = (k, base)
+        dt = torch.float32 if base == 0 else torch.float64
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(5)
+        A = flyte.pack(torch.rand(size * size, dtype=dt, device=dev, generator=gen) * 2 - 1, k)
+        gen.manual_seed(6)
+        B = flyte.pack(torch.rand(size * size, dtype=dt, device=dev, generator=gen) * 2 - 1, k)
+        C = torch.empty(size * size, dtype=dt, device=dev)
+        ws = torch.empty(max(flyte.workspace_bytes("gemm", size, size, size, f), 256), dtype=torch.uint8, device=dev)
+        ms = timeit(lambda: flyte.gemm(size, size, size, A, f, B, f, C=C, ws=ws), reps)
+        useful = 2.0 * size ** 3 / (ms * 1e-3) / 1e12
+        nprod = {2: 1, 3: 4, 4: 6}.get(k, 1)
+        if base == 0:
+            executed = useful * nprod
+            out[f"gemm_f32_k{k}_{size}"] = {"ms": round(ms, 3), "useful_TFLOPs": round(useful, 1),
+                                            "tensor_TFLOPs": round(executed, 1), "bf16_products": nprod,
+                                            "frac_bf16_peak": round(executed / bf16_peak, 4)}
+        else:
+            out[f"gemm_f64_k{k}_{size}"] = {"ms": round(ms, 3), "useful_TFLOPs": round(useful, 3),
+                                            "frac_fp64_nominal": round(useful / fp64_peak, 4)}
+        del A, B, C, ws
+    return out
 
 
 def main():

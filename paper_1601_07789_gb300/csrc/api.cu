@@ -124,16 +124,28 @@ flyte_status flyte_gemm(int64_t m, int64_t n, int64_t k_, double alpha, const vo
                         int64_t lda, const void* B, flyte_fmt fb, int64_t ldb, double beta, void* C,
                         int64_t ldc, void* ws, size_t ws_bytes, cudaStream_t stream) {
   g_error[0] = 0;
-  (void)m; (void)n; (void)k_; (void)alpha; (void)A; (void)fa; (void)lda; (void)B; (void)fb; (void)ldb;
-  (void)beta; (void)C; (void)ldc; (void)ws; (void)ws_bytes; (void)stream;
-  set_error("gemm: not implemented yet");
-  return FLYTE_ERR_UNSUPPORTED;
+  if (!valid_fmt(fa) || !valid_fmt(fb)) return invalid("format (k, base)");
+  if (fa.k != fb.k || fa.base != fb.base) {
+    set_error("gemm: A and B must have the same format");
+    return FLYTE_ERR_UNSUPPORTED;
+  }
+  if (m < 0 || n < 0 || k_ < 0) return invalid("m, n or k < 0");
+  if (lda < (k_ > 1 ? k_ : 1) || ldb < (n > 1 ? n : 1) || ldc < (n > 1 ? n : 1)) return invalid("leading dimension");
+  if (m == 0 || n == 0) return FLYTE_OK;
+  if (!C) return invalid("null C");
+  if (alpha != 0.0 && k_ > 0 && (!A || !B)) return invalid("null A or B");
+  if (m > INT32_MAX / 2 || n > INT32_MAX / 2 || k_ > INT32_MAX / 2) {
+    set_error("gemm: dimensions beyond 2^30 are not supported");
+    return FLYTE_ERR_UNSUPPORTED;
+  }
+  return launch_gemm(m, n, k_, alpha, A, fa, lda, B, ldb, beta, C, ldc, ws, ws_bytes, stream);
 }
 
 size_t flyte_workspace_bytes(const char* op, int64_t m, int64_t n, int64_t k_, flyte_fmt f) {
   (void)k_;
   if (!op || m < 0 || n < 0 || k_ < 0) return size_t(-1);
   if (std::strcmp(op, "dot") == 0) return dot_workspace_bytes(n);
+  if (std::strcmp(op, "gemm") == 0) return gemm_workspace_bytes(m, n, k_, f);
   if (std::strcmp(op, "gemv_n") == 0) return gemv_workspace_bytes('N', m, n, f);
   if (std::strcmp(op, "gemv_t") == 0) return gemv_workspace_bytes('T', m, n, f);
   return size_t(-1);

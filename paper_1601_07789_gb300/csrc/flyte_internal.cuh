@@ -343,5 +343,9 @@ flyte_status launch_dot(double* result, int64_t n, const void* x, flyte_fmt fx, 
 size_t dot_workspace_bytes(int64_t n);
 flyte_status launch_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, int64_t incx, void* y,
                          flyte_fmt fy, int64_t incy, int mode, cudaStream_t s);
+flyte_status launch_gemm(int64_t m, int64_t n, int64_t kdim, double alpha, const void* A, flyte_fmt fa,
+                         int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc, void* ws,
+                         size_t ws_bytes, cudaStream_t s);
+size_t gemm_workspace_bytes(int64_t m, int64_t n, int64_t kdim, flyte_fmt f);
 
 }  // namespace flyte

@@ -1,0 +1,492 @@
+// gemm.cu -- C <- alpha A B + beta C on row-major k-byte operands (Sec. 6, BLAS level 3).
+//
+// Float-based formats run on the tensor cores (tcgen05, bf16 inputs, fp32
+// accumulation in TMEM).  Every float-based flyte value is an exact sum of
+// bf16 "parts": k <= 2 codes are bf16 patterns already (one part), a k = 3
+// value is hi + lo with hi its top 16 bits and lo = v - hi (<= 8 significant
+// bits), and a binary32 (k = 4) value splits into three parts by repeated
+// rounding to bf16.  C is the sum of the part products that matter for the
+// 2^-22 bound: all 4 for k = 3 (hi*hi, hi*lo, lo*hi, lo*lo), 6 of 9 for
+// k = 4 (the dropped ones are below 2^-26 |ab|).
+//
+// A preparation pass writes the parts of A (m x k) and of B transposed
+// (n x k) as K-major bf16 arrays in the workspace; for k = 2 an A whose rows
+// are 16-byte aligned is used in place.  The main kernel is a TMA -> shared
+// memory -> tcgen05.mma pipeline: one thread issues the TMA loads of all
+// parts of a 64-wide k-block into a ring of stages, one thread issues the
+// MMAs (4 per product and k-block, each 128 x BN x 16) into a TMEM
+// accumulator and releases stages with tcgen05.commit, and all four warps
+// then read the accumulator (tcgen05.ld) and apply alpha/beta.  Waits are
+// bounded (bulkpipe.cuh).
+//
+// Double-based formats use binary64 tensor-core MMAs (mma.sync m8n8k4, DMMA)
+// on operands widened to binary64 in shared memory.
+#include <cstring>
+
+#include "tcgen05.cuh"
+
+namespace flyte {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBK = 64;                // bf16 elements per row of a stage tile (128 bytes)
+constexpr int kSmemBudget = 200 * 1024;
+
+// ---- bf16 parts of a float-based value ----------------------------------------------
+
+__device__ __forceinline__ uint16_t bf16_rn(float f) {
+  // round to nearest even; the values split here are finite
+  const uint32_t u = __float_as_uint(f);
+  return uint16_t((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+__device__ __forceinline__ float bf16_to_float(uint16_t b) { return __uint_as_float(uint32_t(b) << 16); }
+
+// NP parts p[0..NP) of the widened value u (a binary32 pattern).
+template <int K, int NP>
+__device__ __forceinline__ void split_parts(uint32_t u, uint16_t (&p)[3]) {
+  if constexpr (K <= 2) {
+    p[0] = uint16_t(u >> 16);                       // the code itself, an exact bf16
+  } else if constexpr (K == 3) {
+    p[0] = uint16_t(u >> 16);                       // hi: top 16 bits
+    const float lo = __fsub_rn(__uint_as_float(u), __uint_as_float(u & 0xFFFF0000u));
+    p[1] = bf16_rn(lo);                             // exact (<= 8 significant bits)
+  } else {
+    const float f = __uint_as_float(u);
+    p[0] = bf16_rn(f);
+    const float r1 = __fsub_rn(f, bf16_to_float(p[0]));
+    p[1] = bf16_rn(r1);
+    const float r2 = __fsub_rn(r1, bf16_to_float(p[1]));
+    p[2] = bf16_rn(r2);
+  }
+}
+
+template <int K>
+__host__ __device__ constexpr int parts_of() { return K <= 2 ? 1 : (K == 3 ? 2 : 3); }
+
+// A (m x k, lda, k-byte codes) -> NP bf16 arrays of m rows x kp, element (i, l) at i*kp + l.
+// Block (x, y) converts 1024 columns of row y.
+template <int K>
+__global__ void __launch_bounds__(256) prep_rows(const uint8_t* __restrict__ A, int64_t lda, int64_t kdim,
+                                                 int64_t kp, uint16_t* __restrict__ out, int64_t part_stride) {
+  constexpr int NP = parts_of<K>();
+  const int64_t i = blockIdx.y;
+  const uint8_t* row = A + i * lda * K;
+  for (int64_t l = int64_t(blockIdx.x) * 1024 + threadIdx.x; l < kdim && l < int64_t(blockIdx.x + 1) * 1024;
+       l += 256) {
+    uint16_t p[3];
+    split_parts<K, NP>(widen<FLYTE_F32, K>(load_code_bytes<K>(row + l * K)), p);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) out[q * part_stride + i * kp + l] = p[q];
+  }
+}
+
+// B (k x n, ldb) -> NP bf16 arrays of n rows x kp (B transposed), via 32 x 32 shared tiles.
+template <int K>
+__global__ void __launch_bounds__(256) prep_cols(const uint8_t* __restrict__ B, int64_t ldb, int64_t kdim,
+                                                 int64_t n, int64_t kp, uint16_t* __restrict__ out,
+                                                 int64_t part_stride) {
+  constexpr int NP = parts_of<K>();
+  __shared__ uint16_t tile[NP][32][33];
+  const int64_t l0 = int64_t(blockIdx.y) * 32, j0 = int64_t(blockIdx.x) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t l = l0 + r, j = j0 + tx;
+    uint16_t p[3] = {0, 0, 0};
+    if (l < kdim && j < n) split_parts<K, NP>(widen<FLYTE_F32, K>(load_code_bytes<K>(B + (l * ldb + j) * K)), p);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) tile[q][r][tx] = p[q];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t j = j0 + r, l = l0 + tx;
+    if (j < n && l < kdim) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q) out[q * part_stride + j * kp + l] = tile[q][tx][r];
+    }
+  }
+}
+
+// ---- the tensor-core kernel ----------------------------------------------------------------
+
+struct PartMaps {
+  CUtensorMap a[3];
+  CUtensorMap b[3];
+};
+
+
+template <int K>
+struct GemmCfg {
+  static constexpr int NP = parts_of<K>();
+  static constexpr int BN = NP == 3 ? 128 : 256;
+  static constexpr int kATile = kBM * kBK * 2;               // bytes of one A part tile
+  static constexpr int kBTile = BN * kBK * 2;
+  static constexpr int kStage = NP * (kATile + kBTile);
+  static constexpr int S = kSmemBudget / kStage > 6 ? 6 : kSmemBudget / kStage;
+  static constexpr int kSmem = 1024 + S * kStage + 256;      // alignment slack, stages, barriers
+  static constexpr int kNProd = NP == 1 ? 1 : (NP == 2 ? 4 : 6);
+  static constexpr int kEpiWarps = 4 * (BN / 64);            // each owns 32 rows x 64 columns
+  static constexpr int kThreads = 32 * (kEpiWarps + 2);      // + producer warp + MMA warp
+  // k-blocks accumulated in TMEM before folding: at most 16-24 MMA steps per chunk
+  static constexpr int kChunkBlocks = NP == 1 ? 4 : 1;
+};
+
+// Part products in issue order: smallest first and the large (0,0) product
+// last, so that only its 4 MMA steps per chunk add into a large partial sum.
+__device__ __constant__ int8_t kProdA[6] = {2, 1, 0, 1, 0, 0};
+__device__ __constant__ int8_t kProdB[6] = {0, 1, 2, 0, 1, 0};
+__device__ __constant__ int8_t kProdA2[4] = {1, 0, 1, 0};
+__device__ __constant__ int8_t kProdB2[4] = {1, 1, 0, 0};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Warps [0, E): epilogue (fold each K chunk's accumulator into fp32 registers,
+// then write C); warp E: TMA producer; warp E + 1: MMA issuer and TMEM owner.
+// The tensor core accumulates a chunk of k-blocks into one of two TMEM
+// buffers while the epilogue warps drain the other.  Its binary32
+// accumulation is biased (measured: errors grow with the number of MMA steps
+// into one accumulator, about one ulp of the partial sum per step), so a
+// chunk holds at most 16 (one product) or 16-24 (split formats) MMA steps and
+// the chunks are added with round-to-nearest in registers.
+template <int K>
+__global__ void __launch_bounds__(GemmCfg<K>::kThreads) gemm_tc_kernel(const __grid_constant__ PartMaps maps,
+                                                                       int64_t m, int64_t n, int64_t kdim,
+                                                                       float alpha, float beta,
+                                                                       float* __restrict__ C, int64_t ldc,
+                                                                       int* __restrict__ status) {
+  using Cfg = GemmCfg<K>;
+  constexpr int NP = Cfg::NP, BN = Cfg::BN, S = Cfg::S, E = Cfg::kEpiWarps;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * Cfg::kStage);
+  uint64_t* empty = full + S;
+  uint64_t* accfull = empty + S;        // 2: chunk accumulator ready
+  uint64_t* accempty = accfull + 2;     // 2: chunk accumulator drained
+  uint64_t* mdone = accempty + 2;       // every MMA has completed
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = int64_t(blockIdx.y) * kBM, n0 = int64_t(blockIdx.x) * BN;
+  const int KB = int((kdim + kBK - 1) / kBK);
+  constexpr int kChunkBlocks = Cfg::kChunkBlocks;
+  const int NC = (KB + kChunkBlocks - 1) / kChunkBlocks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accfull[b], 1);
+      mbar_init(&accempty[b], E);
+    }
+    mbar_init(mdone, 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  if (warp == E + 1) tmem_alloc(tslot, 2 * BN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  auto a_tile = [&](int s, int p) { return smem + s * Cfg::kStage + p * Cfg::kATile; };
+  auto b_tile = [&](int s, int p) { return smem + s * Cfg::kStage + NP * Cfg::kATile + p * Cfg::kBTile; };
+
+  if (warp == E) {
+    if (lane == 0) {
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % S;
+        if (kb >= S && !mbar_wait(&empty[s], uint32_t(((kb / S) - 1) & 1), status)) break;
+        mbar_arrive_expect_tx(&full[s], Cfg::kStage);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) tma_load_2d(a_tile(s, p), &maps.a[p], kb * kBK, int(m0), &full[s]);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) tma_load_2d(b_tile(s, p), &maps.b[p], kb * kBK, int(n0), &full[s]);
+      }
+    }
+  } else if (warp == E + 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = umma_idesc_bf16(kBM, BN);
+      bool ok = true;
+      for (int c = 0; c < NC && ok; ++c) {
+        const int b = c & 1;
+        if (c >= 2 && !mbar_wait(&accempty[b], uint32_t(((c >> 1) - 1) & 1), status)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + uint32_t(b * BN);
+        const int kb_end = min(KB, (c + 1) * kChunkBlocks);
+        for (int kb = c * kChunkBlocks; kb < kb_end; ++kb) {
+          const int s = kb % S;
+          if (!mbar_wait(&full[s], uint32_t((kb / S) & 1), status)) { ok = false; break; }
+          tc_fence_after();
+#pragma unroll
+          for (int q = 0; q < Cfg::kNProd; ++q) {
+            const int pa = NP == 1 ? 0 : (NP == 2 ? kProdA2[q] : kProdA[q]);
+            const int pb = NP == 1 ? 0 : (NP == 2 ? kProdB2[q] : kProdB[q]);
+            const uint64_t ad = umma_desc_kmajor_sw128(smem_addr(a_tile(s, pa)));
+            const uint64_t bd = umma_desc_kmajor_sw128(smem_addr(b_tile(s, pb)));
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk)
+              umma_bf16(acc, ad + 2 * kk, bd + 2 * kk, idesc,
+                        (kb > c * kChunkBlocks || q > 0 || kk > 0) ? 1u : 0u);
+          }
+          umma_commit(&empty[s]);
+        }
+        if (ok) umma_commit(&accfull[b]);
+      }
+      umma_commit(mdone);    // fires once every MMA issued above has completed
+    }
+  } else {
+    // epilogue warp: TMEM lanes 32 * (warp % 4) .. + 31, columns 64 * (warp / 4) .. + 63
+    const int quarter = warp & 3, cblk = warp >> 2;
+    float total[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) total[i] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < NC; ++c) {
+      const int b = c & 1;
+      ok = mbar_wait(&accfull[b], uint32_t((c >> 1) & 1), status);
+      if (!__all_sync(0xFFFFFFFFu, ok)) { ok = false; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint32_t r[16];
+        tmem_ld16(tmem + (uint32_t(32 * quarter) << 16) + uint32_t(b * BN + 64 * cblk + 16 * j), r);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) total[16 * j + i] = __fadd_rn(total[16 * j + i], __uint_as_float(r[i]));
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accempty[b]);
+    }
+    const int64_t row = m0 + 32 * quarter + lane;
+    if (ok && row < m) {
+      float* out = C + row * ldc + n0 + 64 * cblk;
+#pragma unroll
+      for (int i = 0; i < 64; ++i) {
+        if (n0 + 64 * cblk + i < n)
+          out[i] = beta == 0.f ? alpha * total[i] : __fmaf_rn(alpha, total[i], beta * out[i]);
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == E + 1) {
+    // every MMA done (and, after a failed wait, every TMA drained) before TMEM is freed
+    if (lane == 0) {
+      mbar_wait(mdone, 0, nullptr);
+      if (*reinterpret_cast<volatile int*>(status) != 0) {
+        for (int kb = (KB > S ? KB - S : 0); kb < KB; ++kb) mbar_wait(&full[kb % S], uint32_t((kb / S) & 1), nullptr);
+      }
+    }
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 2 * BN);
+  }
+}
+
+// ---- binary64 tensor-core kernel (double-based formats) ------------------------------------------
+
+constexpr int kDT = 64;     // C tile 64 x 64
+constexpr int kDK = 16;     // k step
+
+__device__ __forceinline__ void dmma_884(double (&c)[2], double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+               : "+d"(c[0]), "+d"(c[1])
+               : "d"(a), "d"(b));
+}
+
+// 4 warps, each a 32 x 32 quadrant of the 64 x 64 tile as 4 x 4 blocks of 8 x 8.
+template <int K>
+__global__ void __launch_bounds__(128) gemm_dmma_kernel(const uint8_t* __restrict__ A, int64_t lda,
+                                                        const uint8_t* __restrict__ B, int64_t ldb, int64_t m,
+                                                        int64_t n, int64_t kdim, double alpha, double beta,
+                                                        double* __restrict__ C, int64_t ldc) {
+  __shared__ double sA[kDT][kDK + 1];
+  __shared__ double sB[kDK][kDT + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = int64_t(blockIdx.y) * kDT, n0 = int64_t(blockIdx.x) * kDT;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, t = lane & 3;
+  double acc[4][4][2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+  for (int64_t l0 = 0; l0 < kdim; l0 += kDK) {
+    for (int e = threadIdx.x; e < kDT * kDK; e += 128) {
+      const int r = e / kDK, c = e % kDK;
+      const int64_t i = m0 + r, l = l0 + c;
+      sA[r][c] = (i < m && l < kdim) ? code_to_double<FLYTE_F64, K>(load_code_bytes<K>(A + (i * lda + l) * K)) : 0.0;
+    }
+    for (int e = threadIdx.x; e < kDT * kDK; e += 128) {
+      const int r = e / kDT, c = e % kDT;
+      const int64_t l = l0 + r, j = n0 + c;
+      sB[r][c] = (l < kdim && j < n) ? code_to_double<FLYTE_F64, K>(load_code_bytes<K>(B + (l * ldb + j) * K)) : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kDK; kk += 4) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sA[wm + 8 * i + g][kk + t];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = sB[kk + t][wn + 8 * j + g];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dmma_884(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t row = m0 + wm + 8 * i + g, col = n0 + wn + 8 * j + 2 * t + h;
+        if (row < m && col < n) {
+          double* out = C + row * ldc + col;
+          *out = beta == 0.0 ? alpha * acc[i][j][h] : fma(alpha, acc[i][j][h], beta * *out);
+        }
+      }
+}
+
+__global__ void scale_c(void* C, int64_t m, int64_t n, int64_t ldc, double beta, int is_double) {
+  const int64_t total = m * n;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const int64_t i = t / n, j = t - i * n;
+    if (is_double) {
+      double* c = static_cast<double*>(C) + i * ldc + j;
+      *c = beta == 0.0 ? 0.0 : beta * *c;
+    } else {
+      float* c = static_cast<float*>(C) + i * ldc + j;
+      *c = beta == 0.0 ? 0.f : float(beta) * *c;
+    }
+  }
+}
+
+int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+struct GemmPlan {
+  int np;
+  int64_t kp;            // row stride (elements) of the bf16 part arrays
+  bool a_in_place;       // k = 2 with 16-byte aligned rows: A is used as is
+  int64_t off_status, off_a, off_b, bytes;
+};
+
+GemmPlan plan_gemm(int64_t m, int64_t n, int64_t kdim, flyte_fmt f, const void* A, int64_t lda) {
+  GemmPlan p{};
+  p.off_status = 0;
+  if (f.base == FLYTE_F64) {
+    p.bytes = 16;
+    return p;
+  }
+  p.np = f.k <= 2 ? 1 : (f.k == 3 ? 2 : 3);
+  p.kp = round_up(kdim > 0 ? kdim : 1, 8);
+  p.a_in_place = f.k == 2 && (A == nullptr || reinterpret_cast<uintptr_t>(A) % 16 == 0) && (lda * 2) % 16 == 0;
+  p.off_a = 256;
+  // room for the A parts is reserved even when A is used in place, so that the
+  // size depends on the shape and format only
+  const int64_t a_bytes = round_up(int64_t(p.np) * m * p.kp * 2, 256);
+  p.off_b = p.off_a + a_bytes;
+  p.bytes = p.off_b + round_up(int64_t(p.np) * n * p.kp * 2, 256);
+  return p;
+}
+
+bool encode_map(CUtensorMap* map, const void* ptr, int64_t inner, int64_t outer, int64_t row_bytes, int box_outer) {
+  cuuint64_t dims[2] = {cuuint64_t(inner), cuuint64_t(outer)};
+  cuuint64_t strides[1] = {cuuint64_t(row_bytes)};
+  cuuint32_t box[2] = {cuuint32_t(kBK), cuuint32_t(box_outer)};
+  cuuint32_t es[2] = {1, 1};
+  return cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
+                                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int K>
+flyte_status launch_tc(int64_t m, int64_t n, int64_t kdim, double alpha, const uint8_t* A, int64_t lda,
+                       const uint8_t* B, int64_t ldb, double beta, float* C, int64_t ldc, uint8_t* ws,
+                       const GemmPlan& p, cudaStream_t s) {
+  using Cfg = GemmCfg<K>;
+  int* status = reinterpret_cast<int*>(ws + p.off_status);
+  uint16_t* ap = reinterpret_cast<uint16_t*>(ws + p.off_a);
+  uint16_t* bp = reinterpret_cast<uint16_t*>(ws + p.off_b);
+  if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return cuda_status(cudaGetLastError(), "gemm");
+  if (!p.a_in_place) {
+    dim3 grid(unsigned((kdim + 1023) / 1024), unsigned(m));
+    prep_rows<K><<<grid, 256, 0, s>>>(A, lda, kdim, p.kp, ap, m * p.kp);
+    FLYTE_TRY_LAUNCH("gemm");
+  }
+  {
+    dim3 grid(unsigned((n + 31) / 32), unsigned((kdim + 31) / 32));
+    prep_cols<K><<<grid, 256, 0, s>>>(B, ldb, kdim, n, p.kp, bp, n * p.kp);
+    FLYTE_TRY_LAUNCH("gemm");
+  }
+  PartMaps maps;
+  std::memset(&maps, 0, sizeof(maps));
+  for (int q = 0; q < Cfg::NP; ++q) {
+    const void* abase = p.a_in_place ? static_cast<const void*>(A) : static_cast<const void*>(ap + q * m * p.kp);
+    const int64_t arow = p.a_in_place ? lda * 2 : p.kp * 2;
+    if (!encode_map(&maps.a[q], abase, kdim, m, arow, kBM) ||
+        !encode_map(&maps.b[q], bp + q * n * p.kp, kdim, n, p.kp * 2, Cfg::BN)) {
+      set_error("gemm: cuTensorMapEncodeTiled failed");
+      return FLYTE_ERR_CUDA;
+    }
+  }
+  if (cudaFuncSetAttribute(gemm_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem) !=
+      cudaSuccess)
+    return cuda_status(cudaGetLastError(), "gemm");
+  dim3 grid(unsigned((n + Cfg::BN - 1) / Cfg::BN), unsigned((m + kBM - 1) / kBM));
+  gemm_tc_kernel<K><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(maps, m, n, kdim, float(alpha), float(beta), C, ldc,
+                                                            status);
+  FLYTE_TRY_LAUNCH("gemm");
+  return FLYTE_OK;
+}
+
+}  // namespace
+
+size_t gemm_workspace_bytes(int64_t m, int64_t n, int64_t kdim, flyte_fmt f) {
+  return size_t(plan_gemm(m, n, kdim, f, nullptr, 8).bytes);
+}
+
+flyte_status launch_gemm(int64_t m, int64_t n, int64_t kdim, double alpha, const void* A, flyte_fmt fa,
+                         int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc, void* ws,
+                         size_t ws_bytes, cudaStream_t s) {
+  const bool dbl = fa.base == FLYTE_F64;
+  if (alpha == 0.0 || kdim == 0) {
+    if (beta == 1.0) return FLYTE_OK;
+    scale_c<<<grid_for(m * n, 256), 256, 0, s>>>(C, m, n, ldc, beta, dbl ? 1 : 0);
+    FLYTE_TRY_LAUNCH("gemm");
+    return FLYTE_OK;
+  }
+  const GemmPlan p = plan_gemm(m, n, kdim, fa, A, lda);
+  if (ws == nullptr || ws_bytes < size_t(p.bytes) || reinterpret_cast<uintptr_t>(ws) % 256 != 0) {
+    set_error("gemm: workspace of %lld bytes (256-byte aligned) required", (long long)p.bytes);
+    return FLYTE_ERR_WORKSPACE;
+  }
+  const uint8_t* A8 = static_cast<const uint8_t*>(A);
+  const uint8_t* B8 = static_cast<const uint8_t*>(B);
+  uint8_t* w8 = static_cast<uint8_t*>(ws);
+  if (dbl) {
+    return dispatch_fmt(fa, [&]<int BASE, int K>() -> flyte_status {
+      if constexpr (BASE == FLYTE_F64) {
+        dim3 grid(unsigned((n + kDT - 1) / kDT), unsigned((m + kDT - 1) / kDT));
+        gemm_dmma_kernel<K><<<grid, 128, 0, s>>>(A8, lda, B8, ldb, m, n, kdim, alpha, beta, static_cast<double*>(C),
+                                                 ldc);
+        FLYTE_TRY_LAUNCH("gemm");
+      }
+      return FLYTE_OK;
+    });
+  }
+  switch (fa.k) {
+    case 1: return launch_tc<1>(m, n, kdim, alpha, A8, lda, B8, ldb, beta, static_cast<float*>(C), ldc, w8, p, s);
+    case 2: return launch_tc<2>(m, n, kdim, alpha, A8, lda, B8, ldb, beta, static_cast<float*>(C), ldc, w8, p, s);
+    case 3: return launch_tc<3>(m, n, kdim, alpha, A8, lda, B8, ldb, beta, static_cast<float*>(C), ldc, w8, p, s);
+    case 4: return launch_tc<4>(m, n, kdim, alpha, A8, lda, B8, ldb, beta, static_cast<float*>(C), ldc, w8, p, s);
+  }
+  return FLYTE_ERR_INVALID_ARG;
+}
+
+}  // namespace flyte

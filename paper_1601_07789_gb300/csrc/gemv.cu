@@ -97,6 +97,9 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 #ifndef FLYTE_GEMV_BULK
 #define FLYTE_GEMV_BULK 0
 #endif
+#ifndef FLYTE_GEMV_PREFETCH
+#define FLYTE_GEMV_PREFETCH 0
+#endif
 
 constexpr int kNWarps = 8;
 constexpr int kNRowsPerWarp = 2;
@@ -134,17 +137,39 @@ __global__ void __launch_bounds__(kNWarps * 32) gemv_n_kernel(
 #pragma unroll
       for (int e = 0; e < 4; ++e) dw_zero(acc[r][e]);
     int64_t g = gb + lane;
-    for (; g + 32 * (kNUnroll - 1) < ge; g += 32 * kNUnroll) {
-      float4 xa[kNUnroll], xb[kNUnroll];
-      uint32_t w[kNUnroll][kNRowsPerWarp][K];
+    auto load_batch = [&](int64_t g0, float4 (&xa)[kNUnroll], float4 (&xb)[kNUnroll],
+                          uint32_t (&w)[kNUnroll][kNRowsPerWarp][K]) {
 #pragma unroll
       for (int u = 0; u < kNUnroll; ++u) {
-        const int64_t gu = g + 32 * u;
+        const int64_t gu = g0 + 32 * u;
         xa[u] = __ldg(reinterpret_cast<const float4*>(x1) + gu);
         xb[u] = __ldg(reinterpret_cast<const float4*>(x2) + gu);
 #pragma unroll
         for (int r = 0; r < kNRowsPerWarp; ++r) load_group<K>(rowp[r] + gu * (4 * K), w[u][r]);
       }
+    };
+#if FLYTE_GEMV_PREFETCH
+    float4 nxa[kNUnroll], nxb[kNUnroll];
+    uint32_t nw[kNUnroll][kNRowsPerWarp][K];
+    if (g + 32 * (kNUnroll - 1) < ge) load_batch(g, nxa, nxb, nw);
+#endif
+    for (; g + 32 * (kNUnroll - 1) < ge; g += 32 * kNUnroll) {
+      float4 xa[kNUnroll], xb[kNUnroll];
+      uint32_t w[kNUnroll][kNRowsPerWarp][K];
+#if FLYTE_GEMV_PREFETCH
+#pragma unroll
+      for (int u = 0; u < kNUnroll; ++u) {
+        xa[u] = nxa[u];
+        xb[u] = nxb[u];
+#pragma unroll
+        for (int r = 0; r < kNRowsPerWarp; ++r)
+#pragma unroll
+          for (int j = 0; j < K; ++j) w[u][r][j] = nw[u][r][j];
+      }
+      if (g + 32 * kNUnroll + 32 * (kNUnroll - 1) < ge) load_batch(g + 32 * kNUnroll, nxa, nxb, nw);
+#else
+      load_batch(g, xa, xb, w);
+#endif
 #pragma unroll
       for (int u = 0; u < kNUnroll; ++u) {
         const float xs1[4] = {xa[u].x, xa[u].y, xa[u].z, xa[u].w};
@@ -248,18 +273,38 @@ __global__ void __launch_bounds__(kTThreads) gemv_t_kernel(
       for (int e = 0; e < 4; ++e) dw_zero(acc[h][e]);
     int64_t since = 0;
     int64_t i = i0;
+    auto load_batch = [&](int64_t r, uint32_t (&w)[U][K], float (&b1)[U], float (&b2)[U]) {
+#pragma unroll
+      for (int u = 0; u < U; u += 4) {
+        const float4 p = __ldg(reinterpret_cast<const float4*>(x1 + r + u));
+        const float4 q = __ldg(reinterpret_cast<const float4*>(x2 + r + u));
+        b1[u] = p.x; b1[u + 1] = p.y; b1[u + 2] = p.z; b1[u + 3] = p.w;
+        b2[u] = q.x; b2[u + 1] = q.y; b2[u + 2] = q.z; b2[u + 3] = q.w;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) load_group<K>(colp + (r + u) * lda * K, w[u]);
+    };
+#if FLYTE_GEMV_PREFETCH
+    // software pipeline: the next batch of rows is in flight while this one is folded
+    uint32_t wn[U][K];
+    float n1[U], n2[U];
+    if (i + U <= i1) load_batch(i, wn, n1, n2);
+#endif
     for (; i + U <= i1; i += U) {
       uint32_t w[U][K];
       float a1[U], a2[U];
+#if FLYTE_GEMV_PREFETCH
 #pragma unroll
-      for (int u = 0; u < U; u += 4) {
-        const float4 p = __ldg(reinterpret_cast<const float4*>(x1 + i + u));
-        const float4 q = __ldg(reinterpret_cast<const float4*>(x2 + i + u));
-        a1[u] = p.x; a1[u + 1] = p.y; a1[u + 2] = p.z; a1[u + 3] = p.w;
-        a2[u] = q.x; a2[u + 1] = q.y; a2[u + 2] = q.z; a2[u + 3] = q.w;
+      for (int u = 0; u < U; ++u) {
+        a1[u] = n1[u];
+        a2[u] = n2[u];
+#pragma unroll
+        for (int j = 0; j < K; ++j) w[u][j] = wn[u][j];
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) load_group<K>(colp + (i + u) * lda * K, w[u]);
+      if (i + 2 * U <= i1) load_batch(i + U, wn, n1, n2);
+#else
+      load_batch(i, w, a1, a2);
+#endif
 #pragma unroll
       for (int u = 0; u < U; ++u)
 #pragma unroll
