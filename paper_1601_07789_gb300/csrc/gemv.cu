@@ -81,10 +81,12 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 
 // ---- gemv N ---------------------------------------------------------------------
 
-// Compile-time tuning knobs.  Defaults are the best of a sweep on GB300 at
-// 16384 x 16384 (unroll 2/4 and 4/8 rows per step, bulk pipeline on/off):
-// groups per step in 'N' is 2 for k <= 4 and 4 above; 'T' loads 4 rows per
-// step; the warp-private bulk pipeline is off (slower than direct loads).
+// Compile-time tuning knobs.  Defaults are the best of sweeps on GB300 at
+// 16384 x 16384 (unroll 2/4, 4/8 rows per step, bulk pipeline on/off,
+// software prefetch on/off): groups per step in 'N' is 2 for k <= 4 and 4
+// above, 'N' loads each step just before folding it; 'T' loads 4 rows per
+// step and prefetches the next step while folding the current one; the
+// warp-private bulk pipeline is off (slower than direct loads).
 #ifndef FLYTE_N_UNROLL_SMALL_K
 #define FLYTE_N_UNROLL_SMALL_K 2
 #endif
@@ -97,8 +99,11 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 #ifndef FLYTE_GEMV_BULK
 #define FLYTE_GEMV_BULK 0
 #endif
-#ifndef FLYTE_GEMV_PREFETCH
-#define FLYTE_GEMV_PREFETCH 0
+#ifndef FLYTE_GEMV_PREFETCH_N
+#define FLYTE_GEMV_PREFETCH_N 0
+#endif
+#ifndef FLYTE_GEMV_PREFETCH_T
+#define FLYTE_GEMV_PREFETCH_T 1
 #endif
 
 constexpr int kNWarps = 8;
@@ -148,7 +153,7 @@ __global__ void __launch_bounds__(kNWarps * 32) gemv_n_kernel(
         for (int r = 0; r < kNRowsPerWarp; ++r) load_group<K>(rowp[r] + gu * (4 * K), w[u][r]);
       }
     };
-#if FLYTE_GEMV_PREFETCH
+#if FLYTE_GEMV_PREFETCH_N
     float4 nxa[kNUnroll], nxb[kNUnroll];
     uint32_t nw[kNUnroll][kNRowsPerWarp][K];
     if (g + 32 * (kNUnroll - 1) < ge) load_batch(g, nxa, nxb, nw);
@@ -156,7 +161,7 @@ __global__ void __launch_bounds__(kNWarps * 32) gemv_n_kernel(
     for (; g + 32 * (kNUnroll - 1) < ge; g += 32 * kNUnroll) {
       float4 xa[kNUnroll], xb[kNUnroll];
       uint32_t w[kNUnroll][kNRowsPerWarp][K];
-#if FLYTE_GEMV_PREFETCH
+#if FLYTE_GEMV_PREFETCH_N
 #pragma unroll
       for (int u = 0; u < kNUnroll; ++u) {
         xa[u] = nxa[u];
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(kTThreads) gemv_t_kernel(
 #pragma unroll
       for (int u = 0; u < U; ++u) load_group<K>(colp + (r + u) * lda * K, w[u]);
     };
-#if FLYTE_GEMV_PREFETCH
+#if FLYTE_GEMV_PREFETCH_T
     // software pipeline: the next batch of rows is in flight while this one is folded
     uint32_t wn[U][K];
     float n1[U], n2[U];
@@ -293,7 +298,7 @@ __global__ void __launch_bounds__(kTThreads) gemv_t_kernel(
     for (; i + U <= i1; i += U) {
       uint32_t w[U][K];
       float a1[U], a2[U];
-#if FLYTE_GEMV_PREFETCH
+#if FLYTE_GEMV_PREFETCH_T
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         a1[u] = n1[u];
