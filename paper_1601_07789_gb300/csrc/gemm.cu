@@ -137,10 +137,6 @@ __device__ __constant__ int8_t kProdB[6] = {0, 1, 2, 0, 1, 0};
 __device__ __constant__ int8_t kProdA2[4] = {1, 0, 1, 0};
 __device__ __constant__ int8_t kProdB2[4] = {1, 1, 0, 0};
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
 // Warps [0, E): epilogue (fold each K chunk's accumulator into fp32 registers,
 // then write C); warp E: TMA producer; warp E + 1: MMA issuer and TMEM owner.
 // The tensor core accumulates a chunk of k-blocks into one of two TMEM

@@ -83,10 +83,12 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 
 // Compile-time tuning knobs.  Defaults are the best of sweeps on GB300 at
 // 16384 x 16384 (unroll 2/4, 4/8 rows per step, bulk pipeline on/off,
-// software prefetch on/off): groups per step in 'N' is 2 for k <= 4 and 4
-// above, 'N' loads each step just before folding it; 'T' loads 4 rows per
-// step and prefetches the next step while folding the current one; the
-// warp-private bulk pipeline is off (slower than direct loads).
+// software prefetch on/off, block producer/consumer ring on/off): groups per
+// step in 'N' is 2 for k <= 4 and 4 above, 'N' loads each step just before
+// folding it; 'T' loads 4 rows per step and prefetches the next step while
+// folding the current one; the warp-private bulk pipeline is off (slower
+// than direct loads); the block producer/consumer ring serves 'N' for
+// k <= 4 (k = 4: 0.298 -> 0.254 ms; k = 6 is slower with it).
 #ifndef FLYTE_N_UNROLL_SMALL_K
 #define FLYTE_N_UNROLL_SMALL_K 2
 #endif
@@ -98,6 +100,12 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 #endif
 #ifndef FLYTE_GEMV_BULK
 #define FLYTE_GEMV_BULK 0
+#endif
+#ifndef FLYTE_GEMV_PC
+#define FLYTE_GEMV_PC 1
+#endif
+#ifndef FLYTE_GEMV_PC_KMAX
+#define FLYTE_GEMV_PC_KMAX 4
 #endif
 #ifndef FLYTE_GEMV_PREFETCH_N
 #define FLYTE_GEMV_PREFETCH_N 0
@@ -374,6 +382,173 @@ __global__ void __launch_bounds__(256) gemv_t_finish(const double* __restrict__ 
     double sum = 0.0;
     for (int w = 0; w < 8; ++w) sum += red[w][lane];
     y[j * incy] = epilogue(sum, alpha, beta, y + j * incy);
+  }
+}
+
+// ---- producer/consumer 'N' --------------------------------------------------------------
+//
+// One producer warp streams, per stage, SC columns of x1, x2 and of the
+// block's 16 rows into a ring of shared-memory stages with a few large bulk
+// copies; 8 consumer warps fold the stage from shared memory (2 rows each)
+// and release it.  Registers then hold only accumulators, and the bytes in
+// flight per SM are set by the ring, not by occupancy.
+
+template <int K>
+__host__ __device__ constexpr int pc_cols() { return K <= 4 ? 512 : 256; }            // columns per stage
+template <int K>
+__host__ __device__ constexpr int pc_stage_bytes() { return 8 * pc_cols<K>() + kNRowsPerBlock * pc_cols<K>() * K; }
+template <int K>
+__host__ __device__ constexpr int pc_stages() {
+  // two blocks per SM: each may use (228 KiB - 2 x 1 KiB reserved) / 2, minus barriers
+  constexpr int s = 115456 / pc_stage_bytes<K>();
+  return s < 2 ? 2 : (s > 6 ? 6 : s);
+}
+template <int K>
+__host__ __device__ constexpr int pc_smem() { return pc_stages<K>() * pc_stage_bytes<K>() + 16 * pc_stages<K>() + 128; }
+
+template <int BASE, int K, bool LAZY>
+__global__ void __launch_bounds__((kNWarps + 1) * 32) gemv_n_pc(
+    const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
+    const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t chunk_cols,
+    int64_t nchunks, double* __restrict__ partial, double alpha, double beta, double* __restrict__ y,
+    int64_t incy, int* __restrict__ status) {
+  constexpr int SC = pc_cols<K>();
+  constexpr int S = pc_stages<K>();
+  constexpr int kStage = pc_stage_bytes<K>();
+  constexpr int kRowBytes = SC * K;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * kStage);
+  uint64_t* empty = full + S;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t rb0 = int64_t(blockIdx.x) * kNRowsPerBlock;
+  const int64_t chunk = blockIdx.y;
+  const int64_t cb = chunk * chunk_cols;
+  const int64_t ce = min(n, cb + chunk_cols);
+  const int64_t ge = ce >> 2;
+  // stages cover whole 128-column steps; the rest of the chunk is read directly
+  const int64_t cfull = cb + ((ce - cb) >> 7 << 7);
+  const int NT = int((cfull - cb + SC - 1) / SC);
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], kNWarps);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+
+  if (warp == kNWarps) {
+    // producer
+    for (int t = 0; t < NT; ++t) {
+      const int st = t % S;
+      const int64_t c0 = cb + int64_t(t) * SC;
+      const int cols = int(min(int64_t(SC), cfull - c0));
+      bool ok = true;
+      if (lane == 0 && t >= S) ok = mbar_wait(&empty[st], uint32_t(((t / S) - 1) & 1), status);
+      if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) break;
+      if (lane == 0) mbar_arrive_expect_tx(&full[st], uint32_t(8 * cols + kNRowsPerBlock * cols * K));
+      __syncwarp();
+      uint8_t* d = smem + st * kStage;
+      if (lane < 2 + kNRowsPerBlock) {
+        fence_proxy_async_smem();
+        if (lane == 0) {
+          bulk_g2s(d, x1 + c0, uint32_t(4 * cols), &full[st]);
+        } else if (lane == 1) {
+          bulk_g2s(d + 4 * SC, x2 + c0, uint32_t(4 * cols), &full[st]);
+        } else {
+          const int r = lane - 2;
+          const int64_t row = min(rb0 + r, m - 1);
+          bulk_g2s(d + 8 * SC + r * kRowBytes, A + (row * lda + c0) * K, uint32_t(cols * K), &full[st]);
+        }
+      }
+    }
+    return;
+  }
+
+  // consumer warp: rows row0, row0 + 1
+  const int64_t row0 = rb0 + warp * kNRowsPerWarp;
+  DW acc[kNRowsPerWarp][4];
+  bool ok[kNRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kNRowsPerWarp; ++r) {
+    ok[r] = true;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) dw_zero(acc[r][e]);
+  }
+  bool failed = false;
+  for (int t = 0; t < NT; ++t) {
+    const int st = t % S;
+    const bool got = mbar_wait(&full[st], uint32_t((t / S) & 1), status);
+    if (!__all_sync(0xFFFFFFFFu, got)) { failed = true; break; }
+    const uint8_t* d = smem + st * kStage;
+    const int cols = int(min(int64_t(SC), cfull - (cb + int64_t(t) * SC)));
+    for (int g = lane; g < (cols >> 2); g += 32) {
+      const float4 xa = reinterpret_cast<const float4*>(d)[g];
+      const float4 xb = reinterpret_cast<const float4*>(d + 4 * SC)[g];
+      const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
+      const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+      for (int r = 0; r < kNRowsPerWarp; ++r) {
+        uint32_t w[K];
+        lds_group<K>(d + 8 * SC + (warp * kNRowsPerWarp + r) * kRowBytes + g * 4 * K, w);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+  }
+  if (failed) return;   // the producer stops at its next bounded wait; the status word says why
+  const uint8_t* rowp[kNRowsPerWarp];
+#pragma unroll
+  for (int r = 0; r < kNRowsPerWarp; ++r) rowp[r] = A + min(row0 + r, m - 1) * lda * K;
+  for (int64_t g = (cfull >> 2) + lane; g < ge; g += 32) {
+    const float4 xa = __ldg(reinterpret_cast<const float4*>(x1) + g);
+    const float4 xb = __ldg(reinterpret_cast<const float4*>(x2) + g);
+    const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
+    const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+    for (int r = 0; r < kNRowsPerWarp; ++r) {
+      uint32_t w[K];
+      load_group<K>(rowp[r] + g * (4 * K), w);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
+    }
+  }
+  const int64_t j = (ge << 2) + lane;
+  if (j < ce) {
+#pragma unroll
+    for (int r = 0; r < kNRowsPerWarp; ++r) {
+      const uint64_t q = load_code_bytes<K>(rowp[r] + j * K);
+      fold<BASE, K, LAZY>(widen<BASE, K>(q), x1[j], x2[j], acc[r][0], ok[r]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kNRowsPerWarp; ++r) {
+    double t = 0.0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) t += dw_value(acc[r][e]);
+    t = warp_sum(t);
+    const bool good = __all_sync(0xFFFFFFFFu, ok[r]) && isfinite(t);
+    const int64_t row = row0 + r;
+    if (row >= m) break;
+    if (!good) {
+      const uint8_t* Ar = A + row * lda * K;
+      double s2 = 0.0;
+      for (int64_t c = cb + lane; c < ce; c += 32)
+        s2 = fma(code_to_double<BASE, K>(load_code_bytes<K>(Ar + c * K)), x[c * incx], s2);
+      t = warp_sum(s2);
+    }
+    if (lane == 0) {
+      if (nchunks == 1) {
+        y[row * incy] = epilogue(t, alpha, beta, y + row * incy);
+      } else {
+        partial[row * nchunks + chunk] = t;
+      }
+    }
   }
 }
 
@@ -776,9 +951,24 @@ flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const v
     const uint8_t* A8 = static_cast<const uint8_t*>(A);
     // bulk copies need A and every row start 16-byte aligned
     const bool bulk = FLYTE_GEMV_BULK && fast && reinterpret_cast<uintptr_t>(A) % 16 == 0 && (lda * K) % 16 == 0;
+    const bool pc = FLYTE_GEMV_PC && K <= FLYTE_GEMV_PC_KMAX && fast && reinterpret_cast<uintptr_t>(A) % 16 == 0 &&
+                    (lda * K) % 16 == 0;
     if (trans == 'N') {
       dim3 grid(unsigned((m + kNRowsPerBlock - 1) / kNRowsPerBlock), unsigned(p.nchunks));
-      if (bulk) {
+      if (pc) {
+        constexpr int smem = pc_smem<K>();
+        if (p.lazy) {
+          if (!set_smem_once(gemv_n_pc<BASE, K, true>, smem)) return cuda_status(cudaGetLastError(), "gemv");
+          gemv_n_pc<BASE, K, true><<<grid, (kNWarps + 1) * 32, smem, s>>>(A8, lda, m, n, x1, x2, x, incx,
+                                                                          p.chunk_cols, p.nchunks, part, alpha,
+                                                                          beta, y, incy, status);
+        } else {
+          if (!set_smem_once(gemv_n_pc<BASE, K, false>, smem)) return cuda_status(cudaGetLastError(), "gemv");
+          gemv_n_pc<BASE, K, false><<<grid, (kNWarps + 1) * 32, smem, s>>>(A8, lda, m, n, x1, x2, x, incx,
+                                                                           p.chunk_cols, p.nchunks, part, alpha,
+                                                                           beta, y, incy, status);
+        }
+      } else if (bulk) {
         constexpr int smem = n_bulk_smem<K>();
         if (p.lazy) {
           if (!set_smem_once(gemv_n_bulk<BASE, K, true>, smem)) return cuda_status(cudaGetLastError(), "gemv");
