@@ -23,8 +23,8 @@
  *    last failure of the calling thread.
  *  - Any pointer alignment is accepted; 16-byte aligned pointers (and, for
  *    matrices, rows that start on 16-byte boundaries) take the fast paths.
- *  - Outputs must not overlap inputs, except y in flyte_axpy, which is
- *    updated in place.
+ *  - Outputs must not overlap inputs, except y in flyte_axpy and x in
+ *    flyte_scal, which are updated in place.
  */
 #ifndef FLYTE_H
 #define FLYTE_H
@@ -113,6 +113,14 @@ flyte_status flyte_dot(double* result_dev, int64_t n, const void* x, flyte_fmt f
 flyte_status flyte_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, int64_t incx, void* y,
                         flyte_fmt fy, int64_t incy, flyte_round mode, cudaStream_t stream);
 
+/* scal, in place: x_i <- pack(alpha * x_i, mode), the in-place "scale"
+ * benchmark of Sec. 6 (reads and writes of the stream overlap).  The product
+ * is rounded once in the format's native type: binary64 for double-based,
+ * binary32 (alpha rounded to float) for float-based; then packed as
+ * flyte_pack does.  Bit-exact. */
+flyte_status flyte_scal(int64_t n, double alpha, void* x, flyte_fmt fx, int64_t incx, flyte_round mode,
+                        cudaStream_t stream);
+
 /* ---- BLAS level 2 (Sec. 6.3.2) ----------------------------------------------- */
 
 /* gemv on a row-major k-byte matrix A (m rows, n columns, row i starts at
@@ -127,6 +135,19 @@ flyte_status flyte_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, in
 flyte_status flyte_gemv(char trans, int64_t m, int64_t n, double alpha, const void* A, flyte_fmt fa,
                         int64_t lda, const double* x, int64_t incx, double beta, double* y,
                         int64_t incy, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* gemv with y stored as double-based flytes (fy.base must be FLYTE_F64,
+ * else FLYTE_ERR_UNSUPPORTED; fy.k = 1..8): the write path of Sec. 4.3 and
+ * 5 applied to a BLAS result.  y_i (k bytes at element offset i*incy of the
+ * byte stream y) is read as unpack(y_i) unless beta == 0, the binary64 value
+ * fma(alpha, t_i, beta * unpack(y_i)) is formed as in flyte_gemv, and packed
+ * with `mode` in the same kernel that forms it: the result equals
+ * flyte_pack(flyte_gemv(..., unpack(y), ...)) bit for bit.  alpha == 0 gives
+ * pack(beta * unpack(y)) (beta == 0: zero codes).  Same arguments, workspace
+ * and errors as flyte_gemv otherwise. */
+flyte_status flyte_gemv_packed_y(char trans, int64_t m, int64_t n, double alpha, const void* A, flyte_fmt fa,
+                                 int64_t lda, const double* x, int64_t incx, double beta, void* y, flyte_fmt fy,
+                                 int64_t incy, flyte_round mode, void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /* gemv without a workspace argument.  The paper has no counterpart: this is
  * for callers that cannot allocate device memory themselves (a plug-in inside
@@ -155,14 +176,28 @@ flyte_status flyte_gemv_static(char trans, int64_t m, int64_t n, double alpha, c
  *   float-based k = 3: each value split exactly into two bfloat16 terms, all
  *                      four cross products on tensor cores, FP32 accumulation
  *   float-based k = 4: binary32 inputs split into three bfloat16 terms
- *   double-based k >= 2: binary64 tensor-core (DMMA) products, binary64 C
- *   float-based k = 1: FLYTE_ERR_UNSUPPORTED
+ *   float-based k = 1: the codes are the top byte of a bfloat16 pattern (exact)
+ *   double-based: binary64 tensor-core (DMMA) products, binary64 C
  * C is float for float-based formats and double for double-based ones.
  * Accuracy (float-based): |C - C_exact| <= 2^-22 (|alpha| sum_l |A_il B_lj| + |beta C_ij|);
  * (double-based): 4 k_ 2^-53 (same sums).  beta == 0: C is not read. */
 flyte_status flyte_gemm(int64_t m, int64_t n, int64_t k_, double alpha, const void* A, flyte_fmt fa,
                         int64_t lda, const void* B, flyte_fmt fb, int64_t ldb, double beta, void* C,
                         int64_t ldc, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* gemm with C stored as flytes of the base of A and B (fc.base == fa.base,
+ * else FLYTE_ERR_UNSUPPORTED; fc.k = 1..4 float-based, 1..8 double-based):
+ * C_ij (fc.k bytes at element offset i*ldc + j of the byte stream C) is read
+ * as unpack(C_ij) unless beta == 0, alpha * (A B)_ij + beta * unpack(C_ij) is
+ * formed in C's native type exactly as flyte_gemm forms it, and packed with
+ * `mode` by the thread that formed it (the write path of Sec. 4.3 and 5
+ * fused into the epilogue): the result equals the pack of flyte_gemm's C for
+ * C0 = unpack(C) bit for bit.  Same arguments, workspace and accuracy before
+ * the final rounding as flyte_gemm. */
+flyte_status flyte_gemm_packed_c(int64_t m, int64_t n, int64_t k_, double alpha, const void* A, flyte_fmt fa,
+                                 int64_t lda, const void* B, flyte_fmt fb, int64_t ldb, double beta, void* C,
+                                 flyte_fmt fc, int64_t ldc, flyte_round mode, void* ws, size_t ws_bytes,
+                                 cudaStream_t stream);
 
 /* ---- helpers ---------------------------------------------------------------- */
 

@@ -70,6 +70,8 @@ def lib() -> ctypes.CDLL:
             L.orc_dot.restype = i32
             L.orc_axpy.argtypes = [i64, dbl, vp, i32, i32, i64, vp, i32, i32, i64, i32]
             L.orc_axpy.restype = i32
+            L.orc_scal.argtypes = [i64, dbl, vp, i32, i32, i64, i32]
+            L.orc_scal.restype = i32
             L.orc_gemv.argtypes = [ctypes.c_char, i64, i64, dbl, vp, i32, i32, i64, vp, i64, dbl,
                                    vp, i64, vp]
             L.orc_gemv.restype = i32
@@ -160,6 +162,14 @@ def axpy(n: int, alpha: float, x: np.ndarray, fx: tuple[int, int], incx: int, y:
     _check(lib().orc_axpy(n, alpha, _ptr(x), fx[0], fx[1], incx, _ptr(y), fy[0], fy[1], incy,
                           mode), "axpy")
     return y
+
+
+def scal(n: int, alpha: float, x: np.ndarray, fx: tuple[int, int], incx: int = 1,
+         mode: int = RNE) -> np.ndarray:
+    """Return a copy of stream x after x <- pack(alpha * x)."""
+    x = np.array(x, dtype=np.uint8, copy=True)
+    _check(lib().orc_scal(n, alpha, _ptr(x), fx[0], fx[1], incx, mode), "scal")
+    return x
 
 
 def gemv(trans: str, m: int, n: int, alpha: float, A: np.ndarray, fa: tuple[int, int], lda: int,

@@ -318,6 +318,33 @@ int orc_axpy(int64_t n, double alpha, const uint8_t *x, int bx, int kx, int64_t 
     return 0;
 }
 
+/* ---- scal (the in-place "scale" benchmark of Sec. 6) -------------------- */
+
+/* x_i <- pack(alpha * x_i), in place on the k-byte stream x.  The product is
+ * rounded once in the native type, as in orc_axpy: binary64 for double-based
+ * formats, binary32 with alpha rounded to binary32 for float-based ones. */
+int orc_scal(int64_t n, double alpha, uint8_t *x, int bx, int kx, int64_t incx, int mode)
+{
+    if (!orc_valid(bx, kx) || n < 0 || incx < 1 || mode < 0 || mode > 3) return -1;
+    const float alpha_f = (float)alpha;
+    for (int64_t i = 0; i < n; ++i) {
+        uint8_t *px = x + (size_t)(i * incx) * (size_t)kx;
+        double xi = code_value(bx, kx, px);
+        uint64_t u;
+        if (bx == 0) {
+            float r = alpha_f * (float)xi;
+            uint32_t w;
+            memcpy(&w, &r, 4);
+            u = w;
+        } else {
+            double r = alpha * xi;
+            memcpy(&u, &r, 8);
+        }
+        orc_write_code(px, kx, orc_pack_bits(bx, kx, mode, u));
+    }
+    return 0;
+}
+
 /* ---- gemv (BLAS level 2, Sec. 6.3.2) ------------------------------------ */
 
 /* Row-major A (m x n, leading dimension lda elements, k-byte codes).

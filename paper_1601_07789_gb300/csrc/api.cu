@@ -103,6 +103,18 @@ flyte_status flyte_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, in
   return launch_axpy(n, alpha, x, fx, incx, y, fy, incy, int(mode), stream);
 }
 
+flyte_status flyte_scal(int64_t n, double alpha, void* x, flyte_fmt fx, int64_t incx, flyte_round mode,
+                        cudaStream_t stream) {
+  g_error[0] = 0;
+  if (!valid_fmt(fx)) return invalid("format (k, base)");
+  if (int(mode) < FLYTE_RNE || int(mode) > FLYTE_RTO) return invalid("rounding mode");
+  if (n < 0) return invalid("n < 0");
+  if (incx < 1) return invalid("stride < 1");
+  if (n == 0) return FLYTE_OK;
+  if (!x) return invalid("null pointer");
+  return launch_scal(n, alpha, x, fx, incx, int(mode), stream);
+}
+
 flyte_status flyte_gemv(char trans, int64_t m, int64_t n, double alpha, const void* A, flyte_fmt fa,
                         int64_t lda, const double* x, int64_t incx, double beta, double* y,
                         int64_t incy, void* ws, size_t ws_bytes, cudaStream_t stream) {
@@ -117,7 +129,32 @@ flyte_status flyte_gemv(char trans, int64_t m, int64_t n, double alpha, const vo
   if (m == 0 || n == 0) return FLYTE_OK;
   if (!y) return invalid("null y");
   if (alpha != 0.0 && (!A || !x)) return invalid("null A or x");
-  return launch_gemv(trans, m, n, alpha, A, fa, lda, x, incx, beta, y, incy, ws, ws_bytes, stream);
+  return launch_gemv(trans, m, n, alpha, A, fa, lda, x, incx, beta, y, 0, incy, 0, ws, ws_bytes, stream);
+}
+
+flyte_status flyte_gemv_packed_y(char trans, int64_t m, int64_t n, double alpha, const void* A, flyte_fmt fa,
+                                 int64_t lda, const double* x, int64_t incx, double beta, void* y, flyte_fmt fy,
+                                 int64_t incy, flyte_round mode, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  g_error[0] = 0;
+  if (trans == 'n') trans = 'N';
+  if (trans == 't') trans = 'T';
+  if (trans != 'N' && trans != 'T') return invalid("trans must be 'N' or 'T'");
+  if (!valid_fmt(fa) || !valid_fmt(fy)) return invalid("format (k, base)");
+  if (fy.base != FLYTE_F64) {
+    set_error("gemv_packed_y: y must be double-based (the sums are binary64)");
+    return FLYTE_ERR_UNSUPPORTED;
+  }
+  if (int(mode) < FLYTE_RNE || int(mode) > FLYTE_RTO) return invalid("rounding mode");
+  if (m < 0 || n < 0) return invalid("m < 0 or n < 0");
+  if (lda < (n > 1 ? n : 1)) return invalid("lda < max(1, n)");
+  if (incx < 1 || incy < 1) return invalid("stride < 1");
+  if (m == 0 || n == 0) return FLYTE_OK;
+  if (!y) return invalid("null y");
+  if (alpha != 0.0 && (!A || !x)) return invalid("null A or x");
+  if (fy.k == 8 && reinterpret_cast<uintptr_t>(y) % 8 == 0)   // an aligned binary64 y
+    return launch_gemv(trans, m, n, alpha, A, fa, lda, x, incx, beta, y, 0, incy, 0, ws, ws_bytes, stream);
+  return launch_gemv(trans, m, n, alpha, A, fa, lda, x, incx, beta, y, fy.k, incy, int(mode), ws, ws_bytes,
+                     stream);
 }
 
 flyte_status flyte_gemm(int64_t m, int64_t n, int64_t k_, double alpha, const void* A, flyte_fmt fa,
@@ -138,7 +175,37 @@ flyte_status flyte_gemm(int64_t m, int64_t n, int64_t k_, double alpha, const vo
     set_error("gemm: dimensions beyond 2^30 are not supported");
     return FLYTE_ERR_UNSUPPORTED;
   }
-  return launch_gemm(m, n, k_, alpha, A, fa, lda, B, ldb, beta, C, ldc, ws, ws_bytes, stream);
+  return launch_gemm(m, n, k_, alpha, A, fa, lda, B, ldb, beta, C, 0, ldc, 0, ws, ws_bytes, stream);
+}
+
+flyte_status flyte_gemm_packed_c(int64_t m, int64_t n, int64_t k_, double alpha, const void* A, flyte_fmt fa,
+                                 int64_t lda, const void* B, flyte_fmt fb, int64_t ldb, double beta, void* C,
+                                 flyte_fmt fc, int64_t ldc, flyte_round mode, void* ws, size_t ws_bytes,
+                                 cudaStream_t stream) {
+  g_error[0] = 0;
+  if (!valid_fmt(fa) || !valid_fmt(fb) || !valid_fmt(fc)) return invalid("format (k, base)");
+  if (fa.k != fb.k || fa.base != fb.base) {
+    set_error("gemm: A and B must have the same format");
+    return FLYTE_ERR_UNSUPPORTED;
+  }
+  if (fc.base != fa.base) {
+    set_error("gemm_packed_c: C must have the base of A and B");
+    return FLYTE_ERR_UNSUPPORTED;
+  }
+  if (int(mode) < FLYTE_RNE || int(mode) > FLYTE_RTO) return invalid("rounding mode");
+  if (m < 0 || n < 0 || k_ < 0) return invalid("m, n or k < 0");
+  if (lda < (k_ > 1 ? k_ : 1) || ldb < (n > 1 ? n : 1) || ldc < (n > 1 ? n : 1)) return invalid("leading dimension");
+  if (m == 0 || n == 0) return FLYTE_OK;
+  if (!C) return invalid("null C");
+  if (alpha != 0.0 && k_ > 0 && (!A || !B)) return invalid("null A or B");
+  if (m > INT32_MAX / 2 || n > INT32_MAX / 2 || k_ > INT32_MAX / 2) {
+    set_error("gemm: dimensions beyond 2^30 are not supported");
+    return FLYTE_ERR_UNSUPPORTED;
+  }
+  const int native = fc.base == FLYTE_F64 ? 8 : 4;
+  const int align = fc.base == FLYTE_F64 ? 8 : 4;
+  const int kc = (fc.k == native && reinterpret_cast<uintptr_t>(C) % align == 0) ? 0 : fc.k;   // 0: the native C
+  return launch_gemm(m, n, k_, alpha, A, fa, lda, B, ldb, beta, C, kc, ldc, int(mode), ws, ws_bytes, stream);
 }
 
 size_t flyte_workspace_bytes(const char* op, int64_t m, int64_t n, int64_t k_, flyte_fmt f) {

@@ -14,6 +14,9 @@
 // narrowing is the integer rounding of flyte_pack: the result is bit-exact.
 // Each thread reads and rewrites its own aligned 4k-byte group of y, so the
 // in-place update never has two threads touch the same bytes.
+//
+// scal: x <- pack(alpha * x) in place (the paper's in-place "scale"
+// benchmark, Sec. 6), with the product rounded once in the native type.
 #include "dwacc.cuh"
 
 namespace flyte {
@@ -178,6 +181,48 @@ __global__ void __launch_bounds__(kThreads) axpy_generic(const uint8_t* __restri
   }
 }
 
+// ---- scal ------------------------------------------------------------------------
+
+template <int BASE, int K>
+__device__ __forceinline__ uint64_t scal_one(typename Native<BASE>::bits ux, double alpha, float alpha_f,
+                                             int mode) {
+  if constexpr (BASE == FLYTE_F64) {
+    const double r = __dmul_rn(alpha, __longlong_as_double((long long)ux));
+    return narrow<BASE, K>(uint64_t(__double_as_longlong(r)), mode);
+  } else {
+    const float r = __fmul_rn(alpha_f, __uint_as_float(ux));
+    return narrow<BASE, K>(__float_as_uint(r), mode);
+  }
+}
+
+template <int BASE, int K>
+__global__ void __launch_bounds__(kThreads) scal_groups(uint8_t* __restrict__ X, int64_t ngrp, double alpha,
+                                                        int mode) {
+  const float alpha_f = __double2float_rn(alpha);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngrp; g += stride) {
+    uint32_t wx[K], wo[K];
+    load_group_rw<K>(X + g * (4 * K), wx);
+#pragma unroll
+    for (int j = 0; j < K; ++j) wo[j] = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      deposit_code<K>(wo, e, scal_one<BASE, K>(extract_widened<BASE, K>(wx, e), alpha, alpha_f, mode));
+    store_group<K>(X + g * (4 * K), wo);
+  }
+}
+
+template <int BASE, int K>
+__global__ void __launch_bounds__(kThreads) scal_generic(uint8_t* __restrict__ X, int64_t incx, int64_t first,
+                                                         int64_t n, double alpha, int mode) {
+  const float alpha_f = __double2float_rn(alpha);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = first + int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    uint8_t* p = X + i * incx * K;
+    store_code_bytes<K>(p, scal_one<BASE, K>(widen<BASE, K>(load_code_bytes<K>(p)), alpha, alpha_f, mode));
+  }
+}
+
 bool aligned(const void* p, int bytes) { return reinterpret_cast<uintptr_t>(p) % bytes == 0; }
 
 int dot_blocks(int64_t work) {
@@ -245,6 +290,24 @@ flyte_status launch_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, i
       axpy_generic<BASE, KY><<<grid_for(n - first, kThreads), kThreads, 0, s>>>(X, fx.k, incx, Y, incy, first, n,
                                                                                alpha, mode);
       FLYTE_TRY_LAUNCH("axpy");
+    }
+    return FLYTE_OK;
+  });
+}
+
+flyte_status launch_scal(int64_t n, double alpha, void* x, flyte_fmt fx, int64_t incx, int mode, cudaStream_t s) {
+  uint8_t* X = static_cast<uint8_t*>(x);
+  return dispatch_fmt(fx, [&]<int BASE, int K>() -> flyte_status {
+    int64_t first = 0;
+    if (incx == 1 && aligned(x, group_bytes(K)) && n >= 4) {
+      const int64_t ngrp = n / 4;
+      scal_groups<BASE, K><<<grid_for(ngrp, kThreads), kThreads, 0, s>>>(X, ngrp, alpha, mode);
+      FLYTE_TRY_LAUNCH("scal");
+      first = ngrp * 4;
+    }
+    if (first < n) {
+      scal_generic<BASE, K><<<grid_for(n - first, kThreads), kThreads, 0, s>>>(X, incx, first, n, alpha, mode);
+      FLYTE_TRY_LAUNCH("scal");
     }
     return FLYTE_OK;
   });

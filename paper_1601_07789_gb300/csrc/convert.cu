@@ -79,6 +79,57 @@ __global__ void __launch_bounds__(kThreads) unpack_groups(const uint8_t* __restr
   }
 }
 
+// Double-based unpack with coalesced stores.  A lane's 4 doubles are 32
+// contiguous bytes, so storing them directly makes every 16-byte store of a
+// warp touch 1 KiB with gaps.  Here a warp converts 32 groups (128 elements,
+// 1 KiB of output) at a time, passes them through a per-warp shared buffer
+// (16-byte halves XOR-swizzled so that both the writes and the reads are free
+// of bank conflicts) and stores them with two instructions that each cover
+// 512 contiguous bytes.
+template <int K>
+__global__ void __launch_bounds__(kThreads, K == 4 ? 4 : 1) unpack_f64_tiles(const uint8_t* __restrict__ src,
+                                                             uint8_t* __restrict__ dst, int64_t ntiles) {
+  constexpr int kWarps = kThreads / 32;
+  __shared__ __align__(16) uint4 buf[kWarps][kUnroll][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t wstride = int64_t(gridDim.x) * kWarps;
+  const int sw = (lane >> 2) & 1;
+  for (int64_t t = int64_t(blockIdx.x) * kWarps + warp; t < ntiles; t += kUnroll * wstride) {
+    uint32_t w[kUnroll][K];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t tu = t + u * wstride;
+      if (tu < ntiles) load_group<K>(src + (tu * 32 + lane) * (4 * K), w[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (t + u * wstride < ntiles) {
+        uint64_t v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = extract_widened<FLYTE_F64, K>(w[u], e);
+        buf[warp][u][2 * lane + sw] = make_uint4(uint32_t(v[0]), uint32_t(v[0] >> 32), uint32_t(v[1]),
+                                                 uint32_t(v[1] >> 32));
+        buf[warp][u][2 * lane + (sw ^ 1)] = make_uint4(uint32_t(v[2]), uint32_t(v[2] >> 32), uint32_t(v[3]),
+                                                       uint32_t(v[3] >> 32));
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t tu = t + u * wstride;
+      if (tu < ntiles) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int c = 32 * j + lane;                       // 16-byte chunk of the warp's 1 KiB
+          const uint4 val = buf[warp][u][2 * (c >> 1) + ((c & 1) ^ ((c >> 3) & 1))];
+          reinterpret_cast<uint4*>(dst + tu * 1024)[c] = val;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 template <int BASE, int K>
 __global__ void __launch_bounds__(kThreads) unpack_generic(const uint8_t* __restrict__ src, int64_t inc_src,
                                                            void* __restrict__ dst, int64_t inc_dst,
@@ -128,6 +179,52 @@ __global__ void __launch_bounds__(kThreads) pack_groups(const void* __restrict__
   }
 }
 
+// Double-based pack with coalesced stores, the mirror of unpack_f64_tiles: a
+// lane's 4 codes are 4k bytes at a 4k-byte stride, so storing them directly
+// spreads every store instruction of a warp over 128k bytes (for k = 7 this
+// halved the bandwidth).  A warp packs 32 groups (128 elements) into a
+// per-warp shared buffer and writes the tile's 128k bytes as 16-byte chunks,
+// consecutive lanes taking consecutive chunks.
+template <int K>
+__global__ void __launch_bounds__(kThreads) pack_f64_tiles(const uint8_t* __restrict__ src,
+                                                           uint8_t* __restrict__ dst, int64_t ntiles, int mode) {
+  constexpr int kWarps = kThreads / 32;
+  constexpr int kChunks = 8 * K;                       // 16-byte chunks per tile (128 k bytes)
+  __shared__ __align__(16) uint32_t buf[kWarps][kUnroll][32 * K];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t wstride = int64_t(gridDim.x) * kWarps;
+  for (int64_t t = int64_t(blockIdx.x) * kWarps + warp; t < ntiles; t += kUnroll * wstride) {
+    Quad<FLYTE_F64> q[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t tu = t + u * wstride;
+      if (tu < ntiles) load_quad<FLYTE_F64>(src + (tu * 32 + lane) * 32, q[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (t + u * wstride < ntiles) {
+        uint32_t w[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) w[j] = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) deposit_code<K>(w, e, narrow<FLYTE_F64, K>(q[u].v[e], mode));
+        store_group<K>(reinterpret_cast<uint8_t*>(buf[warp][u]) + lane * (4 * K), w);   // widest aligned stores
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int64_t tu = t + u * wstride;
+      if (tu < ntiles) {
+#pragma unroll
+        for (int c = lane; c < kChunks; c += 32)
+          reinterpret_cast<uint4*>(dst + tu * (128 * K))[c] = reinterpret_cast<const uint4*>(buf[warp][u])[c];
+      }
+    }
+    __syncwarp();
+  }
+}
+
 template <int BASE, int K>
 __global__ void __launch_bounds__(kThreads) pack_generic(const void* __restrict__ src, int64_t inc_src,
                                                          uint8_t* __restrict__ dst, int64_t inc_dst,
@@ -157,12 +254,22 @@ flyte_status launch_unpack(void* dst, const void* src, int64_t n, flyte_fmt f, i
     using Bits = typename Native<BASE>::bits;
     int64_t first = 0;
     const bool fast = inc_src == 1 && inc_dst == 1 && aligned(src, group_bytes(K)) && aligned(dst, 16);
-    if (fast && n >= 4) {
-      const int64_t ngroups = n / 4;
+    if constexpr (BASE == FLYTE_F64 && K < 8) {
+      if (fast && n >= 128) {
+        const int64_t ntiles = n / 128;
+        unpack_f64_tiles<K><<<grid_for(ntiles * 32, kThreads * kUnroll, 6), kThreads, 0, s>>>(
+            static_cast<const uint8_t*>(src), static_cast<uint8_t*>(dst), ntiles);
+        FLYTE_TRY_LAUNCH("unpack");
+        first = ntiles * 128;
+      }
+    }
+    if (fast && n - first >= 4) {
+      const int64_t ngroups = (n - first) / 4;
       unpack_groups<BASE, K><<<grid_for(ngroups, kThreads * kUnroll), kThreads, 0, s>>>(
-          static_cast<const uint8_t*>(src), dst, ngroups);
+          static_cast<const uint8_t*>(src) + first * K, static_cast<uint8_t*>(dst) + first * sizeof(Bits),
+          ngroups);
       FLYTE_TRY_LAUNCH("unpack");
-      first = ngroups * 4;
+      first += ngroups * 4;
     }
     if (first < n) {
       unpack_generic<BASE, K><<<grid_for(n - first, kThreads), kThreads, 0, s>>>(
@@ -178,13 +285,24 @@ flyte_status launch_pack(void* dst, const void* src, int64_t n, flyte_fmt f, int
                          int64_t inc_src, int mode, cudaStream_t s) {
   return dispatch_fmt(f, [&]<int BASE, int K>() -> flyte_status {
     int64_t first = 0;
+    using Bits = typename Native<BASE>::bits;
     const bool fast = inc_src == 1 && inc_dst == 1 && aligned(src, 16) && aligned(dst, group_bytes(K));
-    if (fast && n >= 4) {
-      const int64_t ngroups = n / 4;
+    if constexpr (BASE == FLYTE_F64 && K < 8) {
+      if (fast && aligned(dst, 16) && n >= 128) {
+        const int64_t ntiles = n / 128;
+        pack_f64_tiles<K><<<grid_for(ntiles * 32, kThreads * kUnroll, 6), kThreads, 0, s>>>(
+            static_cast<const uint8_t*>(src), static_cast<uint8_t*>(dst), ntiles, mode);
+        FLYTE_TRY_LAUNCH("pack");
+        first = ntiles * 128;
+      }
+    }
+    if (fast && n - first >= 4) {
+      const int64_t ngroups = (n - first) / 4;
       pack_groups<BASE, K><<<grid_for(ngroups, kThreads * kUnroll), kThreads, 0, s>>>(
-          src, static_cast<uint8_t*>(dst), ngroups, mode);
+          static_cast<const uint8_t*>(src) + first * sizeof(Bits), static_cast<uint8_t*>(dst) + first * K, ngroups,
+          mode);
       FLYTE_TRY_LAUNCH("pack");
-      first = ngroups * 4;
+      first += ngroups * 4;
     }
     if (first < n) {
       pack_generic<BASE, K><<<grid_for(n - first, kThreads), kThreads, 0, s>>>(

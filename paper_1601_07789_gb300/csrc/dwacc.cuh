@@ -70,8 +70,54 @@ __device__ __forceinline__ void dw_add_lazy(DW& acc, float p, float e) {
   acc.hi = s;
 }
 
-// Binary64 value of a double-word accumulator (one rounding at most).
+// Binary64 value of a double-word accumulator (one rounding at most; exact
+// when the pair is normalised, |lo| <= ulp(hi) / 2, since hi + lo then has at
+// most 49 significant bits).
 __device__ __forceinline__ double dw_value(const DW& a) { return double(a.hi) + double(a.lo); }
+
+// Exact renormalisation (TwoSum of the two words): afterwards |lo| <= ulp(hi) / 2.
+// A lazy accumulator can have |lo| > |hi| after cancellation, so the
+// ordering-free TwoSum is used rather than Fast2Sum.
+__device__ __forceinline__ void dw_norm(DW& a) {
+  const float s = __fadd_rn(a.hi, a.lo);
+  const float bp = __fsub_rn(s, a.hi);
+  const float ap = __fsub_rn(s, bp);
+  a.lo = __fadd_rn(__fsub_rn(a.hi, ap), __fsub_rn(a.lo, bp));
+  a.hi = s;
+}
+
+// acc <- acc + b for normalised acc and b: one dw_add step with p = b.hi and
+// e = b.lo (|e| <= u |p|, inside the premises above), so it errs by at most
+// 6 u^2 (|acc| + |b|) and leaves acc normalised.  Combining accumulators in a
+// tree of depth D this way costs at most 6 D u^2 sum|a x| and no binary64
+// instruction (binary64 runs at 1/64 of the binary32 rate on this GPU, and a
+// warp-wide binary64 reduction per row stalled the pipe in profiles).
+__device__ __forceinline__ void dw_add_dw(DW& acc, const DW& b) { dw_add(acc, b.hi, b.lo); }
+
+// Normalise and add the four slot accumulators of a thread: depth 2.
+__device__ __forceinline__ DW dw_sum4(DW a0, DW a1, DW a2, DW a3) {
+  dw_norm(a0);
+  dw_norm(a1);
+  dw_norm(a2);
+  dw_norm(a3);
+  dw_add_dw(a0, a1);
+  dw_add_dw(a2, a3);
+  dw_add_dw(a0, a2);
+  return a0;
+}
+
+// Warp sum of normalised double-word values over an xor tree (depth 5); the
+// value in lane 0 is the one used.
+__device__ __forceinline__ DW dw_warp_sum(DW a) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DW b;
+    b.hi = __shfl_xor_sync(0xFFFFFFFFu, a.hi, o);
+    b.lo = __shfl_xor_sync(0xFFFFFFFFu, a.lo, o);
+    dw_add_dw(a, b);
+  }
+  return a;
+}
 
 // ---- exponent window ------------------------------------------------------
 //
@@ -148,16 +194,18 @@ __device__ __forceinline__ void single_times_x(float a, float x1, float x2, floa
 
 // ---- warp / block reductions in binary64 (fixed order: deterministic) ----------
 
-// True when a length-n dot product summed in chains of at most L terms and
-// combined by a binary64 reduction of depth R meets the bound above.  P is
-// the product-error constant: 14 when one operand is binary64 x = x1 + x2,
-// 20 when both operands are flytes split into high/low pairs (flyte_dot).
-__host__ __device__ constexpr bool dw_bound_ok(int64_t n, int64_t L, int64_t R, int64_t P = 14) {
-  return (6 * L + P) * 32 + R <= 4 * n;
+// True when a length-n dot product summed in chains of at most L terms,
+// combined by a double-word tree of depth D (dw_add_dw) and then by a
+// binary64 reduction of depth R, meets the bound above.  P is the
+// product-error constant: 14 when one operand is binary64 x = x1 + x2, 20
+// when both operands are flytes split into high/low pairs (flyte_dot).
+__host__ __device__ constexpr bool dw_bound_ok(int64_t n, int64_t L, int64_t R, int64_t P = 14, int64_t D = 0) {
+  return (6 * L + P + 6 * D) * 32 + R <= 4 * n;
 }
 // The same for chains accumulated with dw_add_lazy.
-__host__ __device__ constexpr bool dw_lazy_bound_ok(int64_t n, int64_t L, int64_t R, int64_t P = 14) {
-  return (L * L + 13 * L + P) * 32 + R <= 4 * n;
+__host__ __device__ constexpr bool dw_lazy_bound_ok(int64_t n, int64_t L, int64_t R, int64_t P = 14,
+                                                    int64_t D = 0) {
+  return (L * L + 13 * L + P + 6 * D) * 32 + R <= 4 * n;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

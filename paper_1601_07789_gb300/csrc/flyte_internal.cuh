@@ -285,6 +285,30 @@ __device__ __forceinline__ double code_to_double_rt(uint64_t q, int k, int base)
   return double(__uint_as_float(uint32_t(k == 4 ? q : (q << (32 - 8 * k)))));
 }
 
+__device__ __forceinline__ void store_code_bytes_rt(uint8_t* p, uint64_t q, int k) {
+  for (int b = 0; b < k; ++b) p[b] = uint8_t(q >> (8 * b));
+}
+
+// narrow<BASE, k> for a k known only at run time (warp-uniform in every caller).
+template <int BASE>
+__device__ __forceinline__ uint64_t narrow_rt(typename Native<BASE>::bits u, int k, int mode) {
+  switch (k) {
+    case 1: return narrow<BASE, 1>(u, mode);
+    case 2: return narrow<BASE, 2>(u, mode);
+    case 3: return narrow<BASE, 3>(u, mode);
+    case 4: return narrow<BASE, 4>(u, mode);
+  }
+  if constexpr (BASE == FLYTE_F64) {
+    switch (k) {
+      case 5: return narrow<BASE, 5>(u, mode);
+      case 6: return narrow<BASE, 6>(u, mode);
+      case 7: return narrow<BASE, 7>(u, mode);
+      default: return narrow<BASE, 8>(u, mode);
+    }
+  }
+  return uint64_t(u);
+}
+
 // ---- launch geometry -----------------------------------------------------------
 
 int sm_count();   // streaming multiprocessors of the current device (cached per device)
@@ -335,17 +359,18 @@ flyte_status launch_pack(void* dst, const void* src, int64_t n, flyte_fmt f, int
 flyte_status launch_unpack(void* dst, const void* src, int64_t n, flyte_fmt f, int64_t inc_dst,
                            int64_t inc_src, cudaStream_t s);
 flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const void* A, flyte_fmt fa,
-                         int64_t lda, const double* x, int64_t incx, double beta, double* y, int64_t incy,
-                         void* ws, size_t ws_bytes, cudaStream_t s);
+                         int64_t lda, const double* x, int64_t incx, double beta, void* y, int ky, int64_t incy,
+                         int mode, void* ws, size_t ws_bytes, cudaStream_t s);
 size_t gemv_workspace_bytes(char trans, int64_t m, int64_t n, flyte_fmt f);
 flyte_status launch_dot(double* result, int64_t n, const void* x, flyte_fmt fx, int64_t incx, const void* y,
                         flyte_fmt fy, int64_t incy, void* ws, size_t ws_bytes, cudaStream_t s);
 size_t dot_workspace_bytes(int64_t n);
 flyte_status launch_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, int64_t incx, void* y,
                          flyte_fmt fy, int64_t incy, int mode, cudaStream_t s);
+flyte_status launch_scal(int64_t n, double alpha, void* x, flyte_fmt fx, int64_t incx, int mode, cudaStream_t s);
 flyte_status launch_gemm(int64_t m, int64_t n, int64_t kdim, double alpha, const void* A, flyte_fmt fa,
-                         int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc, void* ws,
-                         size_t ws_bytes, cudaStream_t s);
+                         int64_t lda, const void* B, int64_t ldb, double beta, void* C, int kc, int64_t ldc,
+                         int mode, void* ws, size_t ws_bytes, cudaStream_t s);
 size_t gemm_workspace_bytes(int64_t m, int64_t n, int64_t kdim, flyte_fmt f);
 
 }  // namespace flyte

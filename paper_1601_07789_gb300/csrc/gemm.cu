@@ -137,6 +137,47 @@ __device__ __constant__ int8_t kProdB[6] = {0, 1, 2, 0, 1, 0};
 __device__ __constant__ int8_t kProdA2[4] = {1, 0, 1, 0};
 __device__ __constant__ int8_t kProdB2[4] = {1, 1, 0, 0};
 
+// Where C goes: the native array (q == nullptr) or a stream of kc-byte flytes
+// of the same base, packed with `mode` right where the value is formed.
+struct COut {
+  uint8_t* q;
+  int kc, mode;
+};
+
+// C_ij <- alpha acc + beta C_ij (beta == 0: C is not read) at element offset idx.
+__device__ __forceinline__ void store_c(float* C, const COut& co, int64_t idx, float acc, float alpha, float beta) {
+  if (co.q == nullptr) {
+    C[idx] = beta == 0.f ? alpha * acc : __fmaf_rn(alpha, acc, beta * C[idx]);
+    return;
+  }
+  uint8_t* p = co.q + idx * co.kc;
+  float r;
+  if (beta == 0.f) {
+    r = alpha * acc;
+  } else {
+    const uint32_t u = uint32_t(load_code_bytes_rt(p, co.kc) << (32 - 8 * co.kc));
+    r = __fmaf_rn(alpha, acc, beta * __uint_as_float(u));
+  }
+  store_code_bytes_rt(p, narrow_rt<FLYTE_F32>(__float_as_uint(r), co.kc, co.mode), co.kc);
+}
+
+__device__ __forceinline__ void store_c(double* C, const COut& co, int64_t idx, double acc, double alpha,
+                                        double beta) {
+  if (co.q == nullptr) {
+    C[idx] = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * C[idx]);
+    return;
+  }
+  uint8_t* p = co.q + idx * co.kc;
+  double r;
+  if (beta == 0.0) {
+    r = alpha * acc;
+  } else {
+    const uint64_t q = load_code_bytes_rt(p, co.kc);
+    r = fma(alpha, acc, beta * __longlong_as_double((long long)(co.kc == 8 ? q : q << (64 - 8 * co.kc))));
+  }
+  store_code_bytes_rt(p, narrow_rt<FLYTE_F64>(uint64_t(__double_as_longlong(r)), co.kc, co.mode), co.kc);
+}
+
 // Warps [0, E): epilogue (fold each K chunk's accumulator into fp32 registers,
 // then write C); warp E: TMA producer; warp E + 1: MMA issuer and TMEM owner.
 // The tensor core accumulates a chunk of k-blocks into one of two TMEM
@@ -150,7 +191,7 @@ __global__ void __launch_bounds__(GemmCfg<K>::kThreads) gemm_tc_kernel(const __g
                                                                        int64_t m, int64_t n, int64_t kdim,
                                                                        float alpha, float beta,
                                                                        float* __restrict__ C, int64_t ldc,
-                                                                       int* __restrict__ status) {
+                                                                       const COut co, int* __restrict__ status) {
   using Cfg = GemmCfg<K>;
   constexpr int NP = Cfg::NP, BN = Cfg::BN, S = Cfg::S, E = Cfg::kEpiWarps;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -257,11 +298,10 @@ __global__ void __launch_bounds__(GemmCfg<K>::kThreads) gemm_tc_kernel(const __g
     }
     const int64_t row = m0 + 32 * quarter + lane;
     if (ok && row < m) {
-      float* out = C + row * ldc + n0 + 64 * cblk;
+      const int64_t base = row * ldc + n0 + 64 * cblk;
 #pragma unroll
       for (int i = 0; i < 64; ++i) {
-        if (n0 + 64 * cblk + i < n)
-          out[i] = beta == 0.f ? alpha * total[i] : __fmaf_rn(alpha, total[i], beta * out[i]);
+        if (n0 + 64 * cblk + i < n) store_c(C, co, base + i, total[i], alpha, beta);
       }
     }
   }
@@ -296,7 +336,7 @@ template <int K>
 __global__ void __launch_bounds__(128) gemm_dmma_kernel(const uint8_t* __restrict__ A, int64_t lda,
                                                         const uint8_t* __restrict__ B, int64_t ldb, int64_t m,
                                                         int64_t n, int64_t kdim, double alpha, double beta,
-                                                        double* __restrict__ C, int64_t ldc) {
+                                                        double* __restrict__ C, int64_t ldc, const COut co) {
   __shared__ double sA[kDT][kDK + 1];
   __shared__ double sB[kDK][kDT + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -341,25 +381,38 @@ __global__ void __launch_bounds__(128) gemm_dmma_kernel(const uint8_t* __restric
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int64_t row = m0 + wm + 8 * i + g, col = n0 + wn + 8 * j + 2 * t + h;
-        if (row < m && col < n) {
-          double* out = C + row * ldc + col;
-          *out = beta == 0.0 ? alpha * acc[i][j][h] : fma(alpha, acc[i][j][h], beta * *out);
-        }
+        if (row < m && col < n) store_c(C, co, row * ldc + col, acc[i][j][h], alpha, beta);
       }
 }
 
-__global__ void scale_c(void* C, int64_t m, int64_t n, int64_t ldc, double beta, int is_double) {
+// C <- beta C (alpha == 0 or k_ == 0), native or packed; beta == 0 writes zeros without reading C.
+__global__ void scale_c(void* C, int64_t m, int64_t n, int64_t ldc, double beta, int is_double, const COut co) {
   const int64_t total = m * n;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += stride) {
     const int64_t i = t / n, j = t - i * n;
-    if (is_double) {
-      double* c = static_cast<double*>(C) + i * ldc + j;
-      *c = beta == 0.0 ? 0.0 : beta * *c;
-    } else {
-      float* c = static_cast<float*>(C) + i * ldc + j;
-      *c = beta == 0.0 ? 0.f : float(beta) * *c;
+    const int64_t idx = i * ldc + j;
+    if (co.q == nullptr) {
+      if (is_double) {
+        double* c = static_cast<double*>(C) + idx;
+        *c = beta == 0.0 ? 0.0 : beta * *c;
+      } else {
+        float* c = static_cast<float*>(C) + idx;
+        *c = beta == 0.0 ? 0.f : float(beta) * *c;
+      }
+      continue;
     }
+    uint8_t* p = co.q + idx * co.kc;
+    const uint64_t q = beta == 0.0 ? 0 : load_code_bytes_rt(p, co.kc);
+    uint64_t out = 0;
+    if (beta != 0.0 && is_double) {
+      const double r = beta * __longlong_as_double((long long)(co.kc == 8 ? q : q << (64 - 8 * co.kc)));
+      out = narrow_rt<FLYTE_F64>(uint64_t(__double_as_longlong(r)), co.kc, co.mode);
+    } else if (beta != 0.0) {
+      const float r = float(beta) * __uint_as_float(uint32_t(q << (32 - 8 * co.kc)));
+      out = narrow_rt<FLYTE_F32>(__float_as_uint(r), co.kc, co.mode);
+    }
+    store_code_bytes_rt(p, out, co.kc);
   }
 }
 
@@ -391,20 +444,41 @@ GemmPlan plan_gemm(int64_t m, int64_t n, int64_t kdim, flyte_fmt f, const void* 
   return p;
 }
 
+// The driver's tensor-map encoder, looked up through the runtime so that the
+// library does not link libcuda (and loads on machines without a driver).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
 bool encode_map(CUtensorMap* map, const void* ptr, int64_t inner, int64_t outer, int64_t row_bytes, int box_outer) {
+  const EncodeTiledFn encode = encode_tiled_fn();
+  if (encode == nullptr) return false;
   cuuint64_t dims[2] = {cuuint64_t(inner), cuuint64_t(outer)};
   cuuint64_t strides[1] = {cuuint64_t(row_bytes)};
   cuuint32_t box[2] = {cuuint32_t(kBK), cuuint32_t(box_outer)};
   cuuint32_t es[2] = {1, 1};
-  return cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
-                                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int K>
 flyte_status launch_tc(int64_t m, int64_t n, int64_t kdim, double alpha, const uint8_t* A, int64_t lda,
-                       const uint8_t* B, int64_t ldb, double beta, float* C, int64_t ldc, uint8_t* ws,
-                       const GemmPlan& p, cudaStream_t s) {
+                       const uint8_t* B, int64_t ldb, double beta, float* C, int64_t ldc, const COut& co,
+                       uint8_t* ws, const GemmPlan& p, cudaStream_t s) {
   using Cfg = GemmCfg<K>;
   int* status = reinterpret_cast<int*>(ws + p.off_status);
   uint16_t* ap = reinterpret_cast<uint16_t*>(ws + p.off_a);
@@ -436,7 +510,7 @@ flyte_status launch_tc(int64_t m, int64_t n, int64_t kdim, double alpha, const u
     return cuda_status(cudaGetLastError(), "gemm");
   dim3 grid(unsigned((n + Cfg::BN - 1) / Cfg::BN), unsigned((m + kBM - 1) / kBM));
   gemm_tc_kernel<K><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(maps, m, n, kdim, float(alpha), float(beta), C, ldc,
-                                                            status);
+                                                            co, status);
   FLYTE_TRY_LAUNCH("gemm");
   return FLYTE_OK;
 }
@@ -448,12 +522,13 @@ size_t gemm_workspace_bytes(int64_t m, int64_t n, int64_t kdim, flyte_fmt f) {
 }
 
 flyte_status launch_gemm(int64_t m, int64_t n, int64_t kdim, double alpha, const void* A, flyte_fmt fa,
-                         int64_t lda, const void* B, int64_t ldb, double beta, void* C, int64_t ldc, void* ws,
-                         size_t ws_bytes, cudaStream_t s) {
+                         int64_t lda, const void* B, int64_t ldb, double beta, void* C, int kc, int64_t ldc,
+                         int mode, void* ws, size_t ws_bytes, cudaStream_t s) {
   const bool dbl = fa.base == FLYTE_F64;
+  const COut co{kc == 0 ? nullptr : static_cast<uint8_t*>(C), kc, mode};
   if (alpha == 0.0 || kdim == 0) {
     if (beta == 1.0) return FLYTE_OK;
-    scale_c<<<grid_for(m * n, 256), 256, 0, s>>>(C, m, n, ldc, beta, dbl ? 1 : 0);
+    scale_c<<<grid_for(m * n, 256), 256, 0, s>>>(C, m, n, ldc, beta, dbl ? 1 : 0, co);
     FLYTE_TRY_LAUNCH("gemm");
     return FLYTE_OK;
   }
@@ -470,17 +545,18 @@ flyte_status launch_gemm(int64_t m, int64_t n, int64_t kdim, double alpha, const
       if constexpr (BASE == FLYTE_F64) {
         dim3 grid(unsigned((n + kDT - 1) / kDT), unsigned((m + kDT - 1) / kDT));
         gemm_dmma_kernel<K><<<grid, 128, 0, s>>>(A8, lda, B8, ldb, m, n, kdim, alpha, beta, static_cast<double*>(C),
-                                                 ldc);
+                                                 ldc, co);
         FLYTE_TRY_LAUNCH("gemm");
       }
       return FLYTE_OK;
     });
   }
+  float* Cf = static_cast<float*>(C);
   switch (fa.k) {
-    case 1: return launch_tc<1>(m, n, kdim, alpha, A8, lda, B8, ldb, beta, static_cast<float*>(C), ldc, w8, p, s);
-    case 2: return launch_tc<2>(m, n, kdim, alpha, A8, lda, B8, ldb, beta, static_cast<float*>(C), ldc, w8, p, s);
-    case 3: return launch_tc<3>(m, n, kdim, alpha, A8, lda, B8, ldb, beta, static_cast<float*>(C), ldc, w8, p, s);
-    case 4: return launch_tc<4>(m, n, kdim, alpha, A8, lda, B8, ldb, beta, static_cast<float*>(C), ldc, w8, p, s);
+    case 1: return launch_tc<1>(m, n, kdim, alpha, A8, lda, B8, ldb, beta, Cf, ldc, co, w8, p, s);
+    case 2: return launch_tc<2>(m, n, kdim, alpha, A8, lda, B8, ldb, beta, Cf, ldc, co, w8, p, s);
+    case 3: return launch_tc<3>(m, n, kdim, alpha, A8, lda, B8, ldb, beta, Cf, ldc, co, w8, p, s);
+    case 4: return launch_tc<4>(m, n, kdim, alpha, A8, lda, B8, ldb, beta, Cf, ldc, co, w8, p, s);
   }
   return FLYTE_ERR_INVALID_ARG;
 }

@@ -51,6 +51,14 @@ __device__ __forceinline__ void fold(typename Native<BASE>::bits u, float x1, fl
   }
 }
 
+// Sum of a row's four slot accumulators over the warp, in double-word
+// arithmetic (depth 2 + 5), as the binary64 value of lane 0 (exact
+// conversion), broadcast to the warp.
+__device__ __forceinline__ double row_total(const DW (&acc)[4]) {
+  const DW a = dw_warp_sum(dw_sum4(acc[0], acc[1], acc[2], acc[3]));
+  return __shfl_sync(0xFFFFFFFFu, dw_value(a), 0);
+}
+
 __device__ __forceinline__ double epilogue(double t, double alpha, double beta, const double* yp) {
   return beta == 0.0 ? alpha * t : fma(alpha, t, beta * *yp);
 }
@@ -82,13 +90,16 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 // ---- gemv N ---------------------------------------------------------------------
 
 // Compile-time tuning knobs.  Defaults are the best of sweeps on GB300 at
-// 16384 x 16384 (unroll 2/4, 4/8 rows per step, bulk pipeline on/off,
-// software prefetch on/off, block producer/consumer ring on/off): groups per
-// step in 'N' is 2 for k <= 4 and 4 above, 'N' loads each step just before
-// folding it; 'T' loads 4 rows per step and prefetches the next step while
-// folding the current one; the warp-private bulk pipeline is off (slower
-// than direct loads); the block producer/consumer ring serves 'N' for
-// k <= 4 (k = 4: 0.298 -> 0.254 ms; k = 6 is slower with it).
+// 16384 x 16384, double-based k = 3..6:
+//  - 'N' runs the persistent producer/consumer ring below for every k when A
+//    is 16-byte aligned (k = 4: 0.298 -> 0.233 ms, k = 5: 0.377 -> 0.338 ms),
+//    8 consumer warps of 2 rows, 512 columns per stage, tiles of up to 4096
+//    columns (8 warps of 4 rows or 16 warps of 2 rows were slower); the
+//    direct kernel (2 or 4 groups per lane and step) serves the rest;
+//  - 'T' loads 4 rows per step and prefetches the next step while folding
+//    the current one.  A producer/consumer ring for 'T' (8 rows per stage)
+//    was not reliably faster (0.208-0.249 ms at k = 4 against 0.222 ms) and
+//    was dropped, as was a warp-private bulk-copy pipeline for both.
 #ifndef FLYTE_N_UNROLL_SMALL_K
 #define FLYTE_N_UNROLL_SMALL_K 2
 #endif
@@ -98,14 +109,23 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 #ifndef FLYTE_T_ROWS
 #define FLYTE_T_ROWS 4
 #endif
-#ifndef FLYTE_GEMV_BULK
-#define FLYTE_GEMV_BULK 0
-#endif
 #ifndef FLYTE_GEMV_PC
 #define FLYTE_GEMV_PC 1
 #endif
+#ifndef FLYTE_T_FOLD_MAX
+#define FLYTE_T_FOLD_MAX 64            // longest fold period of 'T' (rows, a power of two)
+#endif
 #ifndef FLYTE_GEMV_PC_KMAX
-#define FLYTE_GEMV_PC_KMAX 4
+#define FLYTE_GEMV_PC_KMAX 8
+#endif
+#ifndef FLYTE_PC_COLS_SMALL_K
+#define FLYTE_PC_COLS_SMALL_K 512      // columns per ring stage, k <= 4
+#endif
+#ifndef FLYTE_PC_COLS_LARGE_K
+#define FLYTE_PC_COLS_LARGE_K 512      // columns per ring stage, k > 4
+#endif
+#ifndef FLYTE_PC_CHUNK
+#define FLYTE_PC_CHUNK 4096            // columns per 'N' tile (at most)
 #endif
 #ifndef FLYTE_GEMV_PREFETCH_N
 #define FLYTE_GEMV_PREFETCH_N 0
@@ -117,7 +137,7 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 constexpr int kNWarps = 8;
 constexpr int kNRowsPerWarp = 2;
 constexpr int kNRowsPerBlock = kNWarps * kNRowsPerWarp;
-constexpr int64_t kNChunkCols = 4096;   // columns per chunk, a multiple of 128
+constexpr int64_t kNChunkCols = FLYTE_PC_CHUNK;   // columns per chunk, a multiple of 128
 template <int K>
 __host__ __device__ constexpr int n_unroll() { return K <= 4 ? FLYTE_N_UNROLL_SMALL_K : FLYTE_N_UNROLL_LARGE_K; }
 
@@ -126,7 +146,7 @@ __global__ void __launch_bounds__(kNWarps * 32) gemv_n_kernel(
     const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
     const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t chunk_cols,
     int64_t nchunks, double* __restrict__ partial, double alpha, double beta, double* __restrict__ y,
-    int64_t incy, int fast) {
+    int64_t incy, int fast, int direct) {
   constexpr int kNUnroll = n_unroll<K>();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t row0 = int64_t(blockIdx.x) * kNRowsPerBlock + warp * kNRowsPerWarp;
@@ -218,10 +238,7 @@ __global__ void __launch_bounds__(kNWarps * 32) gemv_n_kernel(
     }
 #pragma unroll
     for (int r = 0; r < kNRowsPerWarp; ++r) {
-      double t = 0.0;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) t += dw_value(acc[r][e]);
-      t = warp_sum(t);
+      const double t = row_total(acc[r]);
       v[r] = t;
       ok[r] = __all_sync(0xFFFFFFFFu, ok[r]) && isfinite(t);
     }
@@ -239,7 +256,7 @@ __global__ void __launch_bounds__(kNWarps * 32) gemv_n_kernel(
       v[r] = warp_sum(s);
     }
     if (lane == 0) {
-      if (nchunks == 1) {
+      if (direct) {
         y[row * incy] = epilogue(v[r], alpha, beta, y + row * incy);
       } else {
         partial[row * nchunks + chunk] = v[r];
@@ -259,10 +276,47 @@ __global__ void __launch_bounds__(256) gemv_n_finish(const double* __restrict__ 
   y[i * incy] = epilogue(t, alpha, beta, y + i * incy);
 }
 
+// The same with y stored as double-based flytes of KY bytes: the epilogue
+// reads the old code (unless beta == 0), forms fma(alpha, t, beta y) in
+// binary64 and packs it with the integer rounding of flyte_pack.
+template <int KY>
+__device__ __forceinline__ void epilogue_packed(double t, double alpha, double beta, uint8_t* yp, int mode) {
+  const double yo = beta == 0.0 ? 0.0 : code_to_double<FLYTE_F64, KY>(load_code_bytes<KY>(yp));
+  const double r = beta == 0.0 ? alpha * t : fma(alpha, t, beta * yo);
+  store_code_bytes<KY>(yp, narrow<FLYTE_F64, KY>(uint64_t(__double_as_longlong(r)), mode));
+}
+
+template <int KY>
+__global__ void __launch_bounds__(256) gemv_n_finish_packed(const double* __restrict__ partial, int64_t nchunks,
+                                                            int64_t m, double alpha, double beta,
+                                                            uint8_t* __restrict__ y, int64_t incy, int mode) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double t = 0.0;
+  for (int64_t c = 0; c < nchunks; ++c) t += partial[i * nchunks + c];
+  epilogue_packed<KY>(t, alpha, beta, y + i * incy * KY, mode);
+}
+
 // ---- gemv T ---------------------------------------------------------------------
 
 constexpr int kTThreads = 128;
 constexpr int kTRowsPerIter = FLYTE_T_ROWS;   // rows loaded per iteration (a multiple of 4)
+
+// Every fold_rows rows the two row-parity chains of each column are
+// renormalised, added, and added into the column's running double-word total
+// (two dw_add_dw levels per fold), then restarted.
+__device__ __forceinline__ void fold_parities(DW (&acc)[2][4], DW (&tot)[4]) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    DW a = acc[0][e], b = acc[1][e];
+    dw_norm(a);
+    dw_norm(b);
+    dw_add_dw(a, b);
+    dw_add_dw(tot[e], a);
+    dw_zero(acc[0][e]);
+    dw_zero(acc[1][e]);
+  }
+}
 
 template <int BASE, int K, bool LAZY>
 __global__ void __launch_bounds__(kTThreads) gemv_t_kernel(
@@ -279,11 +333,13 @@ __global__ void __launch_bounds__(kTThreads) gemv_t_kernel(
   bool ok = fast && c0 + 4 <= n;
   if (ok) {
     const uint8_t* colp = A + c0 * K;
-    DW acc[2][4];
+    DW acc[2][4], tot[4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) dw_zero(acc[h][e]);
+    for (int e = 0; e < 4; ++e) {
+      dw_zero(acc[0][e]);
+      dw_zero(acc[1][e]);
+      dw_zero(tot[e]);
+    }
     int64_t since = 0;
     int64_t i = i0;
     auto load_batch = [&](int64_t r, uint32_t (&w)[U][K], float (&b1)[U], float (&b2)[U]) {
@@ -325,12 +381,7 @@ __global__ void __launch_bounds__(kTThreads) gemv_t_kernel(
           fold<BASE, K, LAZY>(extract_widened<BASE, K>(w[u], e), a1[u], a2[u], acc[u & 1][e], ok);
       since += U;
       if (since >= fold_rows) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          v[e] += dw_value(acc[0][e]) + dw_value(acc[1][e]);
-          dw_zero(acc[0][e]);
-          dw_zero(acc[1][e]);
-        }
+        fold_parities(acc, tot);
         since = 0;
       }
     }
@@ -341,9 +392,10 @@ __global__ void __launch_bounds__(kTThreads) gemv_t_kernel(
 #pragma unroll
       for (int e = 0; e < 4; ++e) fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), a1, a2, acc[0][e], ok);
     }
+    fold_parities(acc, tot);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      v[e] += dw_value(acc[0][e]) + dw_value(acc[1][e]);
+      v[e] = dw_value(tot[e]);      // exact: tot is normalised
       ok = ok && isfinite(v[e]);
     }
   }
@@ -385,33 +437,71 @@ __global__ void __launch_bounds__(256) gemv_t_finish(const double* __restrict__ 
   }
 }
 
+template <int KY>
+__global__ void __launch_bounds__(256) gemv_t_finish_packed(const double* __restrict__ partial, int64_t ntiles,
+                                                            int64_t n, double alpha, double beta,
+                                                            uint8_t* __restrict__ y, int64_t incy, int mode) {
+  __shared__ double red[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t j = int64_t(blockIdx.x) * 32 + lane;
+  double t = 0.0;
+  if (j < n)
+    for (int64_t s = warp; s < ntiles; s += 8) t += partial[s * n + j];
+  red[warp][lane] = t;
+  __syncthreads();
+  if (warp == 0 && j < n) {
+    double sum = 0.0;
+    for (int w = 0; w < 8; ++w) sum += red[w][lane];
+    epilogue_packed<KY>(sum, alpha, beta, y + j * incy * KY, mode);
+  }
+}
+
 // ---- producer/consumer 'N' --------------------------------------------------------------
 //
-// One producer warp streams, per stage, SC columns of x1, x2 and of the
-// block's 16 rows into a ring of shared-memory stages with a few large bulk
-// copies; 8 consumer warps fold the stage from shared memory (2 rows each)
-// and release it.  Registers then hold only accumulators, and the bytes in
-// flight per SM are set by the ring, not by occupancy.
+// A persistent block of kPcWarps consumer warps and one producer warp walks
+// the (row block, column chunk) tiles tau = blockIdx.x, blockIdx.x + grid, ...
+// The producer streams, per stage, SC columns of x1, x2 and of the tile's
+// kPcRowsBlock rows into a ring of shared-memory stages with large bulk
+// copies, running ahead across tile boundaries; the consumers fold each stage
+// from shared memory (kPcRows rows per warp), release it, and at the end of a
+// tile reduce and write their rows.  Registers then hold only accumulators,
+// the bytes in flight per SM are set by the ring rather than by occupancy,
+// and the ring is filled once per block instead of once per tile.
+
+#ifndef FLYTE_PC_WARPS
+#define FLYTE_PC_WARPS 8               // consumer warps per block
+#endif
+#ifndef FLYTE_PC_ROWS
+#define FLYTE_PC_ROWS 2                // rows per consumer warp
+#endif
+#ifndef FLYTE_PC_SMEM
+#define FLYTE_PC_SMEM 115456           // ring budget per block: two blocks per SM
+#endif
+
+constexpr int kPcWarps = FLYTE_PC_WARPS;
+constexpr int kPcRows = FLYTE_PC_ROWS;
+constexpr int kPcRowsBlock = kPcWarps * kPcRows;
+constexpr int kPcThreads = (kPcWarps + 1) * 32;
+static_assert(kPcRowsBlock + 2 <= 64, "the producer warp issues at most two copies per lane and stage");
 
 template <int K>
-__host__ __device__ constexpr int pc_cols() { return K <= 4 ? 512 : 256; }            // columns per stage
+__host__ __device__ constexpr int pc_cols() { return K <= 4 ? FLYTE_PC_COLS_SMALL_K : FLYTE_PC_COLS_LARGE_K; }
 template <int K>
-__host__ __device__ constexpr int pc_stage_bytes() { return 8 * pc_cols<K>() + kNRowsPerBlock * pc_cols<K>() * K; }
+__host__ __device__ constexpr int pc_stage_bytes() { return 8 * pc_cols<K>() + kPcRowsBlock * pc_cols<K>() * K; }
 template <int K>
 __host__ __device__ constexpr int pc_stages() {
-  // two blocks per SM: each may use (228 KiB - 2 x 1 KiB reserved) / 2, minus barriers
-  constexpr int s = 115456 / pc_stage_bytes<K>();
-  return s < 2 ? 2 : (s > 6 ? 6 : s);
+  constexpr int s = FLYTE_PC_SMEM / pc_stage_bytes<K>();
+  return s < 2 ? 2 : (s > 8 ? 8 : s);
 }
 template <int K>
 __host__ __device__ constexpr int pc_smem() { return pc_stages<K>() * pc_stage_bytes<K>() + 16 * pc_stages<K>() + 128; }
 
 template <int BASE, int K, bool LAZY>
-__global__ void __launch_bounds__((kNWarps + 1) * 32) gemv_n_pc(
+__global__ void __launch_bounds__(kPcThreads) gemv_n_pc(
     const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
     const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t chunk_cols,
     int64_t nchunks, double* __restrict__ partial, double alpha, double beta, double* __restrict__ y,
-    int64_t incy, int* __restrict__ status) {
+    int64_t incy, int* __restrict__ status, int direct) {
   constexpr int SC = pc_cols<K>();
   constexpr int S = pc_stages<K>();
   constexpr int kStage = pc_stage_bytes<K>();
@@ -420,423 +510,139 @@ __global__ void __launch_bounds__((kNWarps + 1) * 32) gemv_n_pc(
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * kStage);
   uint64_t* empty = full + S;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t rb0 = int64_t(blockIdx.x) * kNRowsPerBlock;
-  const int64_t chunk = blockIdx.y;
-  const int64_t cb = chunk * chunk_cols;
-  const int64_t ce = min(n, cb + chunk_cols);
-  const int64_t ge = ce >> 2;
-  // stages cover whole 128-column steps; the rest of the chunk is read directly
-  const int64_t cfull = cb + ((ce - cb) >> 7 << 7);
-  const int NT = int((cfull - cb + SC - 1) / SC);
+  const int64_t ntiles = ((m + kPcRowsBlock - 1) / kPcRowsBlock) * nchunks;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], kNWarps);
+      mbar_init(&empty[i], kPcWarps);
     }
     mbar_init_fence();
   }
   __syncthreads();
 
-  if (warp == kNWarps) {
-    // producer
-    for (int t = 0; t < NT; ++t) {
-      const int st = t % S;
-      const int64_t c0 = cb + int64_t(t) * SC;
-      const int cols = int(min(int64_t(SC), cfull - c0));
-      bool ok = true;
-      if (lane == 0 && t >= S) ok = mbar_wait(&empty[st], uint32_t(((t / S) - 1) & 1), status);
-      if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) break;
-      if (lane == 0) mbar_arrive_expect_tx(&full[st], uint32_t(8 * cols + kNRowsPerBlock * cols * K));
-      __syncwarp();
-      uint8_t* d = smem + st * kStage;
-      if (lane < 2 + kNRowsPerBlock) {
+  if (warp == kPcWarps) {
+    // producer: every stage of every tile of this block, in order
+    uint32_t it = 0;
+    for (int64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
+      const int64_t rb0 = (tau / nchunks) * kPcRowsBlock;
+      const int64_t cb = (tau % nchunks) * chunk_cols;
+      const int64_t ce = min(n, cb + chunk_cols);
+      const int64_t cfull = cb + ((ce - cb) >> 7 << 7);   // whole 128-column steps go through the ring
+      for (int64_t c0 = cb; c0 < cfull; c0 += SC, ++it) {
+        const int st = int(it % S);
+        const int cols = int(min(int64_t(SC), cfull - c0));
+        bool ok = true;
+        if (lane == 0 && it >= S) ok = mbar_wait(&empty[st], ((it / S) - 1) & 1, status);
+        if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) return;
+        if (lane == 0) mbar_arrive_expect_tx(&full[st], uint32_t(8 * cols + kPcRowsBlock * cols * K));
+        __syncwarp();
+        uint8_t* d = smem + st * kStage;
         fence_proxy_async_smem();
-        if (lane == 0) {
-          bulk_g2s(d, x1 + c0, uint32_t(4 * cols), &full[st]);
-        } else if (lane == 1) {
-          bulk_g2s(d + 4 * SC, x2 + c0, uint32_t(4 * cols), &full[st]);
-        } else {
-          const int r = lane - 2;
-          const int64_t row = min(rb0 + r, m - 1);
-          bulk_g2s(d + 8 * SC + r * kRowBytes, A + (row * lda + c0) * K, uint32_t(cols * K), &full[st]);
+#pragma unroll
+        for (int c = lane; c < kPcRowsBlock + 2; c += 32) {
+          if (c == 0) {
+            bulk_g2s(d, x1 + c0, uint32_t(4 * cols), &full[st]);
+          } else if (c == 1) {
+            bulk_g2s(d + 4 * SC, x2 + c0, uint32_t(4 * cols), &full[st]);
+          } else {
+            const int r = c - 2;
+            const int64_t row = min(rb0 + r, m - 1);
+            bulk_g2s(d + 8 * SC + r * kRowBytes, A + (row * lda + c0) * K, uint32_t(cols * K), &full[st]);
+          }
         }
       }
     }
     return;
   }
 
-  // consumer warp: rows row0, row0 + 1
-  const int64_t row0 = rb0 + warp * kNRowsPerWarp;
-  DW acc[kNRowsPerWarp][4];
-  bool ok[kNRowsPerWarp];
+  // consumer warp: rows rb0 + warp * kPcRows + r of each tile
+  uint32_t it = 0;
+  for (int64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
+    const int64_t row0 = (tau / nchunks) * kPcRowsBlock + warp * kPcRows;
+    const int64_t chunk = tau % nchunks;
+    const int64_t cb = chunk * chunk_cols;
+    const int64_t ce = min(n, cb + chunk_cols);
+    const int64_t ge = ce >> 2;
+    const int64_t cfull = cb + ((ce - cb) >> 7 << 7);
+    DW acc[kPcRows][4];
+    bool ok[kPcRows];
 #pragma unroll
-  for (int r = 0; r < kNRowsPerWarp; ++r) {
-    ok[r] = true;
+    for (int r = 0; r < kPcRows; ++r) {
+      ok[r] = true;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) dw_zero(acc[r][e]);
-  }
-  bool failed = false;
-  for (int t = 0; t < NT; ++t) {
-    const int st = t % S;
-    const bool got = mbar_wait(&full[st], uint32_t((t / S) & 1), status);
-    if (!__all_sync(0xFFFFFFFFu, got)) { failed = true; break; }
-    const uint8_t* d = smem + st * kStage;
-    const int cols = int(min(int64_t(SC), cfull - (cb + int64_t(t) * SC)));
-    for (int g = lane; g < (cols >> 2); g += 32) {
-      const float4 xa = reinterpret_cast<const float4*>(d)[g];
-      const float4 xb = reinterpret_cast<const float4*>(d + 4 * SC)[g];
+      for (int e = 0; e < 4; ++e) dw_zero(acc[r][e]);
+    }
+    for (int64_t c0 = cb; c0 < cfull; c0 += SC, ++it) {
+      const int st = int(it % S);
+      const bool got = mbar_wait(&full[st], (it / S) & 1, status);
+      if (!__all_sync(0xFFFFFFFFu, got)) return;   // the producer stops at its next bounded wait
+      const uint8_t* d = smem + st * kStage;
+      const int cols = int(min(int64_t(SC), cfull - c0));
+      for (int g = lane; g < (cols >> 2); g += 32) {
+        const float4 xa = reinterpret_cast<const float4*>(d)[g];
+        const float4 xb = reinterpret_cast<const float4*>(d + 4 * SC)[g];
+        const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
+        const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+        for (int r = 0; r < kPcRows; ++r) {
+          uint32_t w[K];
+          lds_group<K>(d + 8 * SC + (warp * kPcRows + r) * kRowBytes + g * 4 * K, w);
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    }
+    const uint8_t* rowp[kPcRows];
+#pragma unroll
+    for (int r = 0; r < kPcRows; ++r) rowp[r] = A + min(row0 + r, m - 1) * lda * K;
+    for (int64_t g = (cfull >> 2) + lane; g < ge; g += 32) {
+      const float4 xa = __ldg(reinterpret_cast<const float4*>(x1) + g);
+      const float4 xb = __ldg(reinterpret_cast<const float4*>(x2) + g);
       const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
       const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
 #pragma unroll
-      for (int r = 0; r < kNRowsPerWarp; ++r) {
+      for (int r = 0; r < kPcRows; ++r) {
         uint32_t w[K];
-        lds_group<K>(d + 8 * SC + (warp * kNRowsPerWarp + r) * kRowBytes + g * 4 * K, w);
+        load_group<K>(rowp[r] + g * (4 * K), w);
 #pragma unroll
         for (int e = 0; e < 4; ++e)
           fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
       }
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[st]);
-  }
-  if (failed) return;   // the producer stops at its next bounded wait; the status word says why
-  const uint8_t* rowp[kNRowsPerWarp];
+    const int64_t j = (ge << 2) + lane;
+    if (j < ce) {
 #pragma unroll
-  for (int r = 0; r < kNRowsPerWarp; ++r) rowp[r] = A + min(row0 + r, m - 1) * lda * K;
-  for (int64_t g = (cfull >> 2) + lane; g < ge; g += 32) {
-    const float4 xa = __ldg(reinterpret_cast<const float4*>(x1) + g);
-    const float4 xb = __ldg(reinterpret_cast<const float4*>(x2) + g);
-    const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
-    const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
-#pragma unroll
-    for (int r = 0; r < kNRowsPerWarp; ++r) {
-      uint32_t w[K];
-      load_group<K>(rowp[r] + g * (4 * K), w);
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
-    }
-  }
-  const int64_t j = (ge << 2) + lane;
-  if (j < ce) {
-#pragma unroll
-    for (int r = 0; r < kNRowsPerWarp; ++r) {
-      const uint64_t q = load_code_bytes<K>(rowp[r] + j * K);
-      fold<BASE, K, LAZY>(widen<BASE, K>(q), x1[j], x2[j], acc[r][0], ok[r]);
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < kNRowsPerWarp; ++r) {
-    double t = 0.0;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) t += dw_value(acc[r][e]);
-    t = warp_sum(t);
-    const bool good = __all_sync(0xFFFFFFFFu, ok[r]) && isfinite(t);
-    const int64_t row = row0 + r;
-    if (row >= m) break;
-    if (!good) {
-      const uint8_t* Ar = A + row * lda * K;
-      double s2 = 0.0;
-      for (int64_t c = cb + lane; c < ce; c += 32)
-        s2 = fma(code_to_double<BASE, K>(load_code_bytes<K>(Ar + c * K)), x[c * incx], s2);
-      t = warp_sum(s2);
-    }
-    if (lane == 0) {
-      if (nchunks == 1) {
-        y[row * incy] = epilogue(t, alpha, beta, y + row * incy);
-      } else {
-        partial[row * nchunks + chunk] = t;
+      for (int r = 0; r < kPcRows; ++r) {
+        const uint64_t q = load_code_bytes<K>(rowp[r] + j * K);
+        fold<BASE, K, LAZY>(widen<BASE, K>(q), x1[j], x2[j], acc[r][0], ok[r]);
       }
     }
-  }
-}
-
-// ---- bulk-pipelined variants ----------------------------------------------------------
-//
-// Same arithmetic as above, but each warp streams its operands through a
-// private ring of S shared-memory stages filled by cp.async.bulk (bulkpipe.cuh)
-// so that S - 1 stages per warp are in flight whatever the occupancy.  Needs
-// A and every row start 16-byte aligned; the launcher checks that.
-
-template <int K>
-__host__ __device__ constexpr int n_stage_bytes() { return 1024 + 2 * 128 * K; }          // x1, x2, two row segments
-template <int K>
-__host__ __device__ constexpr int n_stages() {
-  constexpr int s = 12288 / n_stage_bytes<K>();
-  return s < 3 ? 3 : (s > 8 ? 8 : s);
-}
-template <int K>
-__host__ __device__ constexpr int n_bulk_smem() { return kNWarps * n_stages<K>() * (n_stage_bytes<K>() + 8); }
-
-template <int BASE, int K, bool LAZY>
-__global__ void __launch_bounds__(kNWarps * 32) gemv_n_bulk(
-    const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
-    const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t chunk_cols,
-    int64_t nchunks, double* __restrict__ partial, double alpha, double beta, double* __restrict__ y,
-    int64_t incy, int* __restrict__ status) {
-  constexpr int S = n_stages<K>();
-  constexpr int kStage = n_stage_bytes<K>();
-  extern __shared__ __align__(128) uint8_t smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint8_t* ring = smem + warp * S * kStage;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kNWarps * S * kStage) + warp * S;
-  const int64_t row0 = int64_t(blockIdx.x) * kNRowsPerBlock + warp * kNRowsPerWarp;
-  if (row0 >= m) return;
-  const int64_t chunk = blockIdx.y;
-  const int64_t cb = chunk * chunk_cols;
-  const int64_t ce = min(n, cb + chunk_cols);
-  const int64_t gb = cb >> 2, ge = ce >> 2;
-  const int64_t NI = (ge - gb) >> 5;                   // full 128-column steps, pipelined
-  const uint8_t* rowp[kNRowsPerWarp];
 #pragma unroll
-  for (int r = 0; r < kNRowsPerWarp; ++r) rowp[r] = A + min(row0 + r, m - 1) * lda * K;
-
-  if (lane == 0) {
-    for (int i = 0; i < S; ++i) mbar_init(&bars[i], 1);
-    mbar_init_fence();
-  }
-  __syncwarp();
-  auto issue = [&](int64_t it) {
-    const int st = int(it % S);
-    uint8_t* d = ring + st * kStage;
-    const int64_t g0 = gb + 32 * it;
-    if (lane == 0) mbar_arrive_expect_tx(&bars[st], kStage);
-    __syncwarp();
-    if (lane < 4) {
-      fence_proxy_async_smem();
-      if (lane == 0) bulk_g2s(d, x1 + 4 * g0, 512, &bars[st]);
-      else if (lane == 1) bulk_g2s(d + 512, x2 + 4 * g0, 512, &bars[st]);
-      else bulk_g2s(d + 1024 + (lane - 2) * 128 * K, rowp[lane - 2] + 4 * g0 * K, 128 * K, &bars[st]);
-    }
-  };
-  const int64_t pro = NI < S ? NI : S;
-  for (int64_t it = 0; it < pro; ++it) issue(it);
-
-  DW acc[kNRowsPerWarp][4];
-  bool ok[kNRowsPerWarp];
-#pragma unroll
-  for (int r = 0; r < kNRowsPerWarp; ++r) {
-    ok[r] = true;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) dw_zero(acc[r][e]);
-  }
-  bool failed = false;
-  int64_t it = 0;
-  for (; it < NI; ++it) {
-    const int st = int(it % S);
-    const bool got = mbar_wait(&bars[st], uint32_t((it / S) & 1), status);
-    if (!__all_sync(0xFFFFFFFFu, got)) { failed = true; break; }
-    const uint8_t* d = ring + st * kStage;
-    const float4 xa = reinterpret_cast<const float4*>(d)[lane];
-    const float4 xb = reinterpret_cast<const float4*>(d + 512)[lane];
-    uint32_t w[kNRowsPerWarp][K];
-#pragma unroll
-    for (int r = 0; r < kNRowsPerWarp; ++r) lds_group<K>(d + 1024 + r * 128 * K + lane * 4 * K, w[r]);
-    __syncwarp();
-    if (it + S < NI) issue(it + S);
-    const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
-    const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
-#pragma unroll
-    for (int r = 0; r < kNRowsPerWarp; ++r)
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        fold<BASE, K, LAZY>(extract_widened<BASE, K>(w[r], e), xs1[e], xs2[e], acc[r][e], ok[r]);
-  }
-  if (failed) {
-    // drain the copies still in flight, then give up (the status word says why)
-    for (int64_t j = it; j < NI && j < it + S; ++j) mbar_wait(&bars[j % S], uint32_t((j / S) & 1), nullptr);
-    return;
-  }
-  // groups past the last full step, and the trailing n % 4 elements: direct loads
-  for (int64_t g = gb + 32 * NI + lane; g < ge; g += 32) {
-    const float4 xa = __ldg(reinterpret_cast<const float4*>(x1) + g);
-    const float4 xb = __ldg(reinterpret_cast<const float4*>(x2) + g);
-    const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
-    const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
-#pragma unroll
-    for (int r = 0; r < kNRowsPerWarp; ++r) {
-      uint32_t w[K];
-      load_group<K>(rowp[r] + g * (4 * K), w);
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
-    }
-  }
-  const int64_t j = (ge << 2) + lane;
-  if (j < ce) {
-#pragma unroll
-    for (int r = 0; r < kNRowsPerWarp; ++r) {
-      const uint64_t q = load_code_bytes<K>(rowp[r] + j * K);
-      fold<BASE, K, LAZY>(widen<BASE, K>(q), x1[j], x2[j], acc[r][0], ok[r]);
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < kNRowsPerWarp; ++r) {
-    double t = 0.0;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) t += dw_value(acc[r][e]);
-    t = warp_sum(t);
-    const bool good = __all_sync(0xFFFFFFFFu, ok[r]) && isfinite(t);
-    const int64_t row = row0 + r;
-    if (row >= m) break;
-    if (!good) {
-      const uint8_t* Ar = A + row * lda * K;
-      double s2 = 0.0;
-      for (int64_t c = cb + lane; c < ce; c += 32)
-        s2 = fma(code_to_double<BASE, K>(load_code_bytes<K>(Ar + c * K)), x[c * incx], s2);
-      t = warp_sum(s2);
-    }
-    if (lane == 0) {
-      if (nchunks == 1) {
-        y[row * incy] = epilogue(t, alpha, beta, y + row * incy);
-      } else {
-        partial[row * nchunks + chunk] = t;
+    for (int r = 0; r < kPcRows; ++r) {
+      double t = row_total(acc[r]);
+      const bool good = __all_sync(0xFFFFFFFFu, ok[r]) && isfinite(t);
+      const int64_t row = row0 + r;
+      if (row >= m) break;
+      if (!good) {
+        const uint8_t* Ar = A + row * lda * K;
+        double s2 = 0.0;
+        for (int64_t c = cb + lane; c < ce; c += 32)
+          s2 = fma(code_to_double<BASE, K>(load_code_bytes<K>(Ar + c * K)), x[c * incx], s2);
+        t = warp_sum(s2);
       }
-    }
-  }
-}
-
-template <int K>
-__host__ __device__ constexpr int t_stage_bytes() { return 64 + kTRowsPerIter * 128 * K; }   // x1[8], x2[8], 8 row segments
-template <int K>
-__host__ __device__ constexpr int t_stages() {
-  constexpr int s = 16384 / t_stage_bytes<K>();
-  return s < 3 ? 3 : (s > 6 ? 6 : s);
-}
-template <int K>
-__host__ __device__ constexpr int t_bulk_smem() { return (kTThreads / 32) * t_stages<K>() * (t_stage_bytes<K>() + 8); }
-
-template <int BASE, int K, bool LAZY>
-__global__ void __launch_bounds__(kTThreads) gemv_t_bulk(
-    const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
-    const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t rb,
-    int64_t fold_rows, double* __restrict__ partial, int* __restrict__ status) {
-  constexpr int U = kTRowsPerIter;
-  constexpr int S = t_stages<K>();
-  constexpr int kStage = t_stage_bytes<K>();
-  constexpr int kWarps = kTThreads / 32;
-  extern __shared__ __align__(128) uint8_t smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint8_t* ring = smem + warp * S * kStage;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kWarps * S * kStage) + warp * S;
-  const int64_t c0w = (int64_t(blockIdx.x) * kWarps + warp) * 128;
-  if (c0w >= n) return;
-  const int64_t c0 = c0w + 4 * lane;
-  const int64_t i0 = int64_t(blockIdx.y) * rb;
-  const int64_t i1 = min(m, i0 + rb);
-  const bool whole = c0w + 128 <= n;                   // the warp's 128 columns all exist
-  const int64_t NI = whole ? (i1 - i0) / U : 0;
-  const uint8_t* colw = A + c0w * K;
-
-  if (lane == 0) {
-    for (int i = 0; i < S; ++i) mbar_init(&bars[i], 1);
-    mbar_init_fence();
-  }
-  __syncwarp();
-  auto issue = [&](int64_t it) {
-    const int st = int(it % S);
-    uint8_t* d = ring + st * kStage;
-    const int64_t r0 = i0 + U * it;
-    if (lane == 0) mbar_arrive_expect_tx(&bars[st], kStage);
-    __syncwarp();
-    if (lane < U + 2) {
-      fence_proxy_async_smem();
-      if (lane == 0) bulk_g2s(d, x1 + r0, 32, &bars[st]);
-      else if (lane == 1) bulk_g2s(d + 32, x2 + r0, 32, &bars[st]);
-      else bulk_g2s(d + 64 + (lane - 2) * 128 * K, colw + (r0 + lane - 2) * lda * K, 128 * K, &bars[st]);
-    }
-  };
-  const int64_t pro = NI < S ? NI : S;
-  for (int64_t it = 0; it < pro; ++it) issue(it);
-
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  bool ok = c0 + 4 <= n;
-  DW acc[2][4];
-#pragma unroll
-  for (int h = 0; h < 2; ++h)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) dw_zero(acc[h][e]);
-  int64_t since = 0;
-  bool failed = false;
-  int64_t it = 0;
-  for (; it < NI; ++it) {
-    const int st = int(it % S);
-    const bool got = mbar_wait(&bars[st], uint32_t((it / S) & 1), status);
-    if (!__all_sync(0xFFFFFFFFu, got)) { failed = true; break; }
-    const uint8_t* d = ring + st * kStage;
-    float a1[U], a2[U];
-#pragma unroll
-    for (int u = 0; u < U; u += 4) {
-      const float4 p = reinterpret_cast<const float4*>(d)[u / 4];
-      const float4 q = reinterpret_cast<const float4*>(d + 32)[u / 4];
-      a1[u] = p.x; a1[u + 1] = p.y; a1[u + 2] = p.z; a1[u + 3] = p.w;
-      a2[u] = q.x; a2[u + 1] = q.y; a2[u + 2] = q.z; a2[u + 3] = q.w;
-    }
-    uint32_t w[U][K];
-#pragma unroll
-    for (int u = 0; u < U; ++u) lds_group<K>(d + 64 + u * 128 * K + lane * 4 * K, w[u]);
-    __syncwarp();
-    if (it + S < NI) issue(it + S);
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int e = 0; e < 4; ++e)
-        fold<BASE, K, LAZY>(extract_widened<BASE, K>(w[u], e), a1[u], a2[u], acc[u & 1][e], ok);
-    since += U;
-    if (since >= fold_rows) {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        v[e] += dw_value(acc[0][e]) + dw_value(acc[1][e]);
-        dw_zero(acc[0][e]);
-        dw_zero(acc[1][e]);
-      }
-      since = 0;
-    }
-  }
-  if (failed) {
-    for (int64_t j = it; j < NI && j < it + S; ++j) mbar_wait(&bars[j % S], uint32_t((j / S) & 1), nullptr);
-    return;
-  }
-  if (ok) {
-    // rows past the last full step (and every row of a partial warp): direct loads
-    for (int64_t i = i0 + U * NI; i < i1; ++i) {
-      uint32_t w[K];
-      load_group<K>(A + (i * lda + c0) * K, w);
-      const float a1 = x1[i], a2 = x2[i];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), a1, a2, acc[i & 1][e], ok);
-      if (++since >= fold_rows) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          v[e] += dw_value(acc[0][e]) + dw_value(acc[1][e]);
-          dw_zero(acc[0][e]);
-          dw_zero(acc[1][e]);
+      if (lane == 0) {
+        if (direct) {
+          y[row * incy] = epilogue(t, alpha, beta, y + row * incy);
+        } else {
+          partial[row * nchunks + chunk] = t;
         }
-        since = 0;
       }
     }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      v[e] += dw_value(acc[0][e]) + dw_value(acc[1][e]);
-      ok = ok && isfinite(v[e]);
-    }
   }
-  if (!ok) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      double s2 = 0.0;
-      if (c0 + e < n) {
-        for (int64_t i = i0; i < i1; ++i)
-          s2 = fma(code_to_double<BASE, K>(load_code_bytes<K>(A + (i * lda + c0 + e) * K)), x[i * incx], s2);
-      }
-      v[e] = s2;
-    }
-  }
-  double* out = partial + int64_t(blockIdx.y) * n + c0;
-#pragma unroll
-  for (int e = 0; e < 4; ++e)
-    if (c0 + e < n) out[e] = v[e];
 }
 
 __global__ void scale_y(double* __restrict__ y, int64_t len, int64_t incy, double beta) {
@@ -866,39 +672,55 @@ struct Plan {
 Plan plan_gemv(char trans, int64_t m, int64_t n) {
   Plan p{};
   const int64_t lenx = trans == 'N' ? n : m;
-  p.off_status = 0;                   // int: error bits of the bulk pipelines
+  p.off_status = 0;                   // int: error bits of the bulk-copy pipeline
   p.off_x1 = 16;
   p.off_x2 = p.off_x1 + align16(4 * lenx);
   p.off_part = p.off_x2 + align16(4 * lenx);
   if (trans == 'N') {
-    // chunks of at most kNChunkCols columns (whole 128-column warp steps)
-    p.nchunks = (n + kNChunkCols - 1) / kNChunkCols;
-    p.chunk_cols = (((n + p.nchunks - 1) / p.nchunks) + 127) / 128 * 128;
-    p.nchunks = (n + p.chunk_cols - 1) / p.chunk_cols;
-    // chain: one term per 128-column step (+ one trailing element); reduction:
-    // 4 slots, 5 warp levels and the chunks
-    const int64_t L = p.chunk_cols / 128 + 1;
-    const int64_t R = 3 + 5 + p.nchunks + 1;
-    p.lazy = dw_lazy_bound_ok(n, L, R);
-    p.fast = p.lazy || dw_bound_ok(n, L, R);
-    p.bytes = p.off_part + (p.nchunks > 1 ? 8 * m * p.nchunks : 0);
+    // Chunks of at most kNChunkCols columns (whole 128-column warp steps),
+    // halved while that lets the chains use the lazy accumulator.  Chain: one
+    // term per 128-column step (+ one trailing element); double-word tree: 4
+    // slots (2 levels) and 5 warp levels; binary64: the chunks.
+    // Prefer the widest lazy plan, then the widest fast one.
+    p.fast = p.lazy = false;
+    bool have = false;
+    for (int64_t cmax = kNChunkCols; cmax >= 512 && !p.lazy; cmax /= 2) {
+      Plan q = p;
+      q.nchunks = (n + cmax - 1) / cmax;
+      q.chunk_cols = (((n + q.nchunks - 1) / q.nchunks) + 127) / 128 * 128;
+      q.nchunks = (n + q.chunk_cols - 1) / q.chunk_cols;
+      const int64_t L = q.chunk_cols / 128 + 1;
+      const int64_t D = 2 + 5;
+      const int64_t R = q.nchunks + 1;
+      q.lazy = dw_lazy_bound_ok(n, L, R, 14, D);
+      q.fast = q.lazy || dw_bound_ok(n, L, R, 14, D);
+      if (!have || q.lazy || (q.fast && !p.fast)) {
+        p = q;
+        have = true;
+      }
+    }
+    p.bytes = p.off_part + 8 * m * p.nchunks;   // partial sums (also for one chunk with a packed y)
   } else {
     p.rb = kTRowTile;
     p.ntiles = (m + p.rb - 1) / p.rb;
     // chain: fold_rows / 2 rows per parity (+ up to kTRowsPerIter trailing
-    // rows); reduction: parities, folds of a tile and the tiles
-    const int64_t R = 2 + p.rb / kTRowsPerIter + p.ntiles + 2;
+    // rows); double-word: the parity sum and one total per fold (the folds of
+    // the tile plus the trailing one); binary64: the tiles in gemv_t_finish
+    // (at most ntiles / 8 + 8 additions in a row)
+    const int64_t R = p.ntiles / 8 + 8 + 1;
     p.lazy = false;
     p.fast = false;
     p.fold_rows = p.rb;
-    for (int64_t f = 64; f >= kTRowsPerIter && !p.fast; f /= 2) {
-      if (dw_lazy_bound_ok(m, f / 2 + kTRowsPerIter, R)) {
+    auto depth = [&](int64_t f) { return 1 + (p.rb + f - 1) / f + 1; };
+    constexpr int64_t kTrail = kTRowsPerIter;   // terms per parity after the last fold (trailing rows)
+    for (int64_t f = FLYTE_T_FOLD_MAX; f >= kTRowsPerIter && !p.fast; f /= 2) {
+      if (dw_lazy_bound_ok(m, f / 2 + kTrail, R, 14, depth(f))) {
         p.fast = p.lazy = true;
         p.fold_rows = f;
       }
     }
     for (int64_t f = p.rb; f >= kTRowsPerIter && !p.fast; f /= 2) {
-      if (dw_bound_ok(m, f / 2 + kTRowsPerIter, R)) {
+      if (dw_bound_ok(m, f / 2 + kTrail, R, 14, depth(f))) {
         p.fast = true;
         p.fold_rows = f;
       }
@@ -915,15 +737,69 @@ size_t gemv_workspace_bytes(char trans, int64_t m, int64_t n, flyte_fmt f) {
   return size_t(plan_gemv(trans, m, n).bytes);
 }
 
+namespace {
+
+template <int KY>
+__global__ void scale_y_packed(uint8_t* __restrict__ y, int64_t len, int64_t incy, double beta, int mode) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < len; j += stride) {
+    uint8_t* p = y + j * incy * KY;
+    if (beta == 0.0) {
+      store_code_bytes<KY>(p, 0);
+    } else {
+      const double r = beta * code_to_double<FLYTE_F64, KY>(load_code_bytes<KY>(p));
+      store_code_bytes<KY>(p, narrow<FLYTE_F64, KY>(uint64_t(__double_as_longlong(r)), mode));
+    }
+  }
+}
+
+// Epilogue launch: y <- alpha t + beta y from the partial sums, as binary64
+// (ky == 0) or packed to ky-byte double-based flytes.
+flyte_status finish_y(char trans, const double* part, int64_t parts, int64_t len, double alpha, double beta,
+                      void* y, int ky, int64_t incy, int mode, cudaStream_t s) {
+  const bool N = trans == 'N';
+  const unsigned grid = N ? unsigned((len + 255) / 256) : unsigned((len + 31) / 32);
+  if (ky == 0) {
+    if (N) {
+      gemv_n_finish<<<grid, 256, 0, s>>>(part, parts, len, alpha, beta, static_cast<double*>(y), incy);
+    } else {
+      gemv_t_finish<<<grid, 256, 0, s>>>(part, parts, len, alpha, beta, static_cast<double*>(y), incy);
+    }
+  } else {
+    const flyte_fmt fy{ky, FLYTE_F64};
+    return dispatch_fmt(fy, [&]<int BASE, int KY>() -> flyte_status {
+      uint8_t* y8 = static_cast<uint8_t*>(y);
+      if (N) {
+        gemv_n_finish_packed<KY><<<grid, 256, 0, s>>>(part, parts, len, alpha, beta, y8, incy, mode);
+      } else {
+        gemv_t_finish_packed<KY><<<grid, 256, 0, s>>>(part, parts, len, alpha, beta, y8, incy, mode);
+      }
+      FLYTE_TRY_LAUNCH("gemv");
+      return FLYTE_OK;
+    });
+  }
+  FLYTE_TRY_LAUNCH("gemv");
+  return FLYTE_OK;
+}
+
+}  // namespace
+
 flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const void* A, flyte_fmt fa,
-                         int64_t lda, const double* x, int64_t incx, double beta, double* y, int64_t incy,
-                         void* ws, size_t ws_bytes, cudaStream_t s) {
+                         int64_t lda, const double* x, int64_t incx, double beta, void* yv, int ky, int64_t incy,
+                         int mode, void* ws, size_t ws_bytes, cudaStream_t s) {
   const int64_t leny = trans == 'N' ? m : n;
   if (alpha == 0.0) {
     if (beta == 1.0) return FLYTE_OK;
-    scale_y<<<grid_for(leny, 256), 256, 0, s>>>(y, leny, incy, beta);
-    FLYTE_TRY_LAUNCH("gemv");
-    return FLYTE_OK;
+    if (ky == 0) {
+      scale_y<<<grid_for(leny, 256), 256, 0, s>>>(static_cast<double*>(yv), leny, incy, beta);
+      FLYTE_TRY_LAUNCH("gemv");
+      return FLYTE_OK;
+    }
+    return dispatch_fmt(flyte_fmt{ky, FLYTE_F64}, [&]<int BASE, int KY>() -> flyte_status {
+      scale_y_packed<KY><<<grid_for(leny, 256), 256, 0, s>>>(static_cast<uint8_t*>(yv), leny, incy, beta, mode);
+      FLYTE_TRY_LAUNCH("gemv");
+      return FLYTE_OK;
+    });
   }
   const Plan p = plan_gemv(trans, m, n);
   if (ws == nullptr || ws_bytes < size_t(p.bytes)) {
@@ -940,7 +816,10 @@ flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const v
   float* x2 = reinterpret_cast<float*>(w8 + p.off_x2);
   double* part = reinterpret_cast<double*>(w8 + p.off_part);
   const int64_t lenx = trans == 'N' ? n : m;
-  return dispatch_fmt(fa, [&]<int BASE, int K>() -> flyte_status {
+  // the 'N' kernels write y themselves for one chunk and a binary64 y
+  const int direct = (trans == 'N' && p.nchunks == 1 && ky == 0) ? 1 : 0;
+  double* y = static_cast<double*>(yv);
+  const flyte_status st = dispatch_fmt(fa, [&]<int BASE, int K>() -> flyte_status {
     constexpr int S = group_bytes(K);
     const bool aligned = reinterpret_cast<uintptr_t>(A) % S == 0 && (lda * K) % S == 0;
     const int fast = (p.fast && aligned) ? 1 : 0;
@@ -949,63 +828,39 @@ flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const v
       FLYTE_TRY_LAUNCH("gemv");
     }
     const uint8_t* A8 = static_cast<const uint8_t*>(A);
-    // bulk copies need A and every row start 16-byte aligned
-    const bool bulk = FLYTE_GEMV_BULK && fast && reinterpret_cast<uintptr_t>(A) % 16 == 0 && (lda * K) % 16 == 0;
+    // the producer's bulk copies need A and every row start 16-byte aligned
     const bool pc = FLYTE_GEMV_PC && K <= FLYTE_GEMV_PC_KMAX && fast && reinterpret_cast<uintptr_t>(A) % 16 == 0 &&
                     (lda * K) % 16 == 0;
     if (trans == 'N') {
       dim3 grid(unsigned((m + kNRowsPerBlock - 1) / kNRowsPerBlock), unsigned(p.nchunks));
       if (pc) {
         constexpr int smem = pc_smem<K>();
-        if (p.lazy) {
-          if (!set_smem_once(gemv_n_pc<BASE, K, true>, smem)) return cuda_status(cudaGetLastError(), "gemv");
-          gemv_n_pc<BASE, K, true><<<grid, (kNWarps + 1) * 32, smem, s>>>(A8, lda, m, n, x1, x2, x, incx,
-                                                                          p.chunk_cols, p.nchunks, part, alpha,
-                                                                          beta, y, incy, status);
-        } else {
-          if (!set_smem_once(gemv_n_pc<BASE, K, false>, smem)) return cuda_status(cudaGetLastError(), "gemv");
-          gemv_n_pc<BASE, K, false><<<grid, (kNWarps + 1) * 32, smem, s>>>(A8, lda, m, n, x1, x2, x, incx,
-                                                                           p.chunk_cols, p.nchunks, part, alpha,
-                                                                           beta, y, incy, status);
-        }
-      } else if (bulk) {
-        constexpr int smem = n_bulk_smem<K>();
-        if (p.lazy) {
-          if (!set_smem_once(gemv_n_bulk<BASE, K, true>, smem)) return cuda_status(cudaGetLastError(), "gemv");
-          gemv_n_bulk<BASE, K, true><<<grid, kNWarps * 32, smem, s>>>(A8, lda, m, n, x1, x2, x, incx, p.chunk_cols,
-                                                                      p.nchunks, part, alpha, beta, y, incy, status);
-        } else {
-          if (!set_smem_once(gemv_n_bulk<BASE, K, false>, smem)) return cuda_status(cudaGetLastError(), "gemv");
-          gemv_n_bulk<BASE, K, false><<<grid, kNWarps * 32, smem, s>>>(A8, lda, m, n, x1, x2, x, incx,
-                                                                       p.chunk_cols, p.nchunks, part, alpha, beta, y,
-                                                                       incy, status);
-        }
+        const int64_t ntiles = ((m + kPcRowsBlock - 1) / kPcRowsBlock) * p.nchunks;
+        auto run = [&](auto kern) -> flyte_status {
+          if (!set_smem_once(kern, smem)) return cuda_status(cudaGetLastError(), "gemv");
+          int per_sm = 0;
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPcThreads, smem) != cudaSuccess)
+            return cuda_status(cudaGetLastError(), "gemv");
+          const int64_t blocks = min(ntiles, int64_t(max(per_sm, 1)) * sm_count());
+          kern<<<unsigned(blocks), kPcThreads, smem, s>>>(A8, lda, m, n, x1, x2, x, incx, p.chunk_cols, p.nchunks,
+                                                         part, alpha, beta, y, incy, status, direct);
+          return FLYTE_OK;
+        };
+        const flyte_status st = p.lazy ? run(gemv_n_pc<BASE, K, true>) : run(gemv_n_pc<BASE, K, false>);
+        if (st != FLYTE_OK) return st;
       } else if (p.lazy) {
         gemv_n_kernel<BASE, K, true><<<grid, kNWarps * 32, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.chunk_cols,
-                                                                   p.nchunks, part, alpha, beta, y, incy, fast);
+                                                                   p.nchunks, part, alpha, beta, y, incy, fast,
+                                                                   direct);
       } else {
         gemv_n_kernel<BASE, K, false><<<grid, kNWarps * 32, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.chunk_cols,
-                                                                    p.nchunks, part, alpha, beta, y, incy, fast);
+                                                                    p.nchunks, part, alpha, beta, y, incy, fast,
+                                                                    direct);
       }
       FLYTE_TRY_LAUNCH("gemv");
-      if (p.nchunks > 1) {
-        gemv_n_finish<<<unsigned((m + 255) / 256), 256, 0, s>>>(part, p.nchunks, m, alpha, beta, y, incy);
-        FLYTE_TRY_LAUNCH("gemv");
-      }
     } else {
       dim3 grid(unsigned((n + 4 * kTThreads - 1) / (4 * kTThreads)), unsigned(p.ntiles));
-      if (bulk) {
-        constexpr int smem = t_bulk_smem<K>();
-        if (p.lazy) {
-          if (!set_smem_once(gemv_t_bulk<BASE, K, true>, smem)) return cuda_status(cudaGetLastError(), "gemv");
-          gemv_t_bulk<BASE, K, true><<<grid, kTThreads, smem, s>>>(A8, lda, m, n, x1, x2, x, incx, p.rb, p.fold_rows,
-                                                                   part, status);
-        } else {
-          if (!set_smem_once(gemv_t_bulk<BASE, K, false>, smem)) return cuda_status(cudaGetLastError(), "gemv");
-          gemv_t_bulk<BASE, K, false><<<grid, kTThreads, smem, s>>>(A8, lda, m, n, x1, x2, x, incx, p.rb,
-                                                                    p.fold_rows, part, status);
-        }
-      } else if (p.lazy) {
+      if (p.lazy) {
         gemv_t_kernel<BASE, K, true><<<grid, kTThreads, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.rb, p.fold_rows,
                                                                 part, fast);
       } else {
@@ -1013,11 +868,11 @@ flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const v
                                                                  p.fold_rows, part, fast);
       }
       FLYTE_TRY_LAUNCH("gemv");
-      gemv_t_finish<<<unsigned((n + 31) / 32), 256, 0, s>>>(part, p.ntiles, n, alpha, beta, y, incy);
-      FLYTE_TRY_LAUNCH("gemv");
     }
     return FLYTE_OK;
   });
+  if (st != FLYTE_OK || direct) return st;
+  return finish_y(trans, part, trans == 'N' ? p.nchunks : p.ntiles, leny, alpha, beta, yv, ky, incy, mode, s);
 }
 
 }  // namespace flyte

@@ -26,8 +26,9 @@ STATUS = {0: "FLYTE_OK", 1: "FLYTE_ERR_INVALID_ARG", 2: "FLYTE_ERR_UNSUPPORTED",
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libflyte.so")
 
 # every entry point declared in include/flyte.h
-EXPORTS = ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_gemv", "flyte_gemv_static",
-           "flyte_gemm", "flyte_workspace_bytes", "flyte_last_error_string", "flyte_version")
+EXPORTS = ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_scal", "flyte_gemv",
+           "flyte_gemv_packed_y", "flyte_gemv_static", "flyte_gemm", "flyte_gemm_packed_c",
+           "flyte_workspace_bytes", "flyte_last_error_string", "flyte_version")
 
 
 class FlyteError(RuntimeError):
@@ -69,14 +70,20 @@ def lib() -> ctypes.CDLL:
             L.flyte_unpack.argtypes = [vp, vp, i64, Fmt, i64, i64, vp]
             L.flyte_dot.argtypes = [vp, i64, vp, Fmt, i64, vp, Fmt, i64, vp, sz, vp]
             L.flyte_axpy.argtypes = [i64, dbl, vp, Fmt, i64, vp, Fmt, i64, i32, vp]
+            L.flyte_scal.argtypes = [i64, dbl, vp, Fmt, i64, i32, vp]
+            L.flyte_gemv_packed_y.argtypes = [ctypes.c_char, i64, i64, dbl, vp, Fmt, i64, vp, i64, dbl,
+                                              vp, Fmt, i64, i32, vp, sz, vp]
             L.flyte_gemv.argtypes = [ctypes.c_char, i64, i64, dbl, vp, Fmt, i64, vp, i64, dbl, vp,
                                      i64, vp, sz, vp]
             L.flyte_gemv_static.argtypes = [ctypes.c_char, i64, i64, dbl, vp, Fmt, i64, vp, i64, dbl,
                                             vp, i64, vp]
             L.flyte_gemm.argtypes = [i64, i64, i64, dbl, vp, Fmt, i64, vp, Fmt, i64, dbl, vp, i64,
                                      vp, sz, vp]
-            for name in ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_gemv",
-                         "flyte_gemv_static", "flyte_gemm"):
+            L.flyte_gemm_packed_c.argtypes = [i64, i64, i64, dbl, vp, Fmt, i64, vp, Fmt, i64, dbl, vp, Fmt,
+                                              i64, i32, vp, sz, vp]
+            for name in ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_scal",
+                         "flyte_gemv", "flyte_gemv_packed_y", "flyte_gemv_static", "flyte_gemm",
+                         "flyte_gemm_packed_c"):
                 getattr(L, name).restype = i32
             L.flyte_workspace_bytes.argtypes = [ctypes.c_char_p, i64, i64, i64, Fmt]
             L.flyte_workspace_bytes.restype = sz
@@ -189,6 +196,16 @@ def axpy(alpha: float, x: torch.Tensor, fx, y: torch.Tensor, fy, n: int | None =
     return y
 
 
+def scal(alpha: float, x: torch.Tensor, fx, n: int | None = None, incx: int = 1, mode="rne",
+         stream=None) -> torch.Tensor:
+    """In place: x <- pack(alpha * x) on a flyte stream; returns x."""
+    fx = fmt(fx)
+    if n is None:
+        n = (x.numel() // fx.k + incx - 1) // incx
+    _check(lib().flyte_scal(n, float(alpha), _ptr(x), fx, incx, _mode(mode), _stream(stream)))
+    return x
+
+
 def gemv_raw(trans: str, m: int, n: int, alpha: float, A, fa, lda: int, x, incx: int,
              beta: float, y, incy: int, ws, ws_bytes: int, stream=None):
     _check(lib().flyte_gemv(trans.encode(), m, n, float(alpha), _ptr(A), fmt(fa), lda, _ptr(x),
@@ -208,6 +225,14 @@ def gemv(trans: str, m: int, n: int, alpha: float, A: torch.Tensor, fa, lda: int
     return y
 
 
+def gemv_packed_y_raw(trans: str, m: int, n: int, alpha: float, A, fa, lda: int, x, incx: int,
+                      beta: float, y, fy, incy: int, mode, ws, ws_bytes: int, stream=None):
+    """gemv whose y is a stream of double-based flytes of format fy (packed in the epilogue)."""
+    _check(lib().flyte_gemv_packed_y(trans.encode(), m, n, float(alpha), _ptr(A), fmt(fa), lda, _ptr(x),
+                                     incx, float(beta), _ptr(y), fmt(fy), incy, _mode(mode), _ptr(ws),
+                                     ws_bytes, _stream(stream)))
+
+
 def gemv_static_raw(trans: str, m: int, n: int, alpha: float, A, fa, lda: int, x, incx: int,
                     beta: float, y, incy: int, stream=None):
     """gemv with the library's built-in scratch (no workspace; see flyte_gemv_static)."""
@@ -219,6 +244,14 @@ def gemm_raw(m: int, n: int, k: int, alpha: float, A, fa, lda: int, B, fb, ldb: 
              C, ldc: int, ws, ws_bytes: int, stream=None):
     _check(lib().flyte_gemm(m, n, k, float(alpha), _ptr(A), fmt(fa), lda, _ptr(B), fmt(fb), ldb,
                             float(beta), _ptr(C), ldc, _ptr(ws), ws_bytes, _stream(stream)))
+
+
+def gemm_packed_c_raw(m: int, n: int, k: int, alpha: float, A, fa, lda: int, B, fb, ldb: int, beta: float,
+                      C, fc, ldc: int, mode, ws, ws_bytes: int, stream=None):
+    """gemm whose C is a stream of flytes of format fc (packed in the epilogue)."""
+    _check(lib().flyte_gemm_packed_c(m, n, k, float(alpha), _ptr(A), fmt(fa), lda, _ptr(B), fmt(fb), ldb,
+                                     float(beta), _ptr(C), fmt(fc), ldc, _mode(mode), _ptr(ws), ws_bytes,
+                                     _stream(stream)))
 
 
 def gemm(m: int, n: int, k: int, A: torch.Tensor, fa, B: torch.Tensor, fb,

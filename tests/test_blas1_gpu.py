@@ -1,7 +1,7 @@
-"""GPU parity of flyte_dot and flyte_axpy against the CPU oracle.
+"""GPU parity of flyte_dot, flyte_axpy and flyte_scal against the CPU oracle.
 
 dot: |s_gpu - s_ref| <= 4 n 2^-53 sum|x_i y_i| + 2^-52 |s_ref| (s_ref is the
-oracle's Dot2); Inf/NaN results must match in class.  axpy: bit-exact codes,
+oracle's Dot2); Inf/NaN results must match in class.  axpy and scal: bit-exact codes,
 except that a NaN result only has to be a NaN code (the GPU's fma returns a
 canonical NaN while the CPU propagates the payload).
 """
@@ -190,3 +190,59 @@ def test_axpy_rejects_mixed_bases():
     with pytest.raises(flyte.FlyteError) as e:
         flyte.axpy(1.0, buf, (4, 1), buf, (2, 0), n=4)
     assert e.value.status == 2
+
+
+# ---- scal (in place) --------------------------------------------------------------
+
+def run_scal(n, alpha, xs, fx, incx, mode, x_off=0):
+    X = Guarded(xs.size, x_off, fill=xs)
+    flyte._check(flyte.lib().flyte_scal(n, float(alpha), X.ptr, flyte.fmt(fx), incx, flyte._mode(mode),
+                                        flyte._stream(None)))
+    sync()
+    X.check_guards()
+    return X.inner()
+
+
+def check_scal(got, n, alpha, xs, fx, incx, mode):
+    want = oracle.scal(n, alpha, xs, fx[::-1], incx, ORC_MODE[mode])
+    if np.array_equal(got, want):
+        return
+    k, base = fx
+    gb = oracle.unpack(got, base, k, n=n, inc_src=incx)
+    wb = oracle.unpack(want, base, k, n=n, inc_src=incx)
+    gv = gb.view(np.float32 if base == 0 else np.float64)
+    wv = wb.view(np.float32 if base == 0 else np.float64)
+    diff = gb != wb
+    assert np.all(np.isnan(gv[diff]) & np.isnan(wv[diff])), f"{diff.sum()} codes differ"
+    mask = np.ones(got.size, bool)
+    for i in range(n):
+        mask[i * incx * k: i * incx * k + k] = False
+    assert np.array_equal(got[mask], xs[mask])
+
+
+@pytest.mark.parametrize("f", FORMATS, ids=lambda f: f"k{f[0]}{'d' if f[1] else 'f'}")
+@pytest.mark.parametrize("mode", MODES)
+def test_scal_sizes(f, mode):
+    g = np.random.default_rng(f[0] + 37 * f[1])
+    for n in [1, 3, 4, 5, 130, 4099, 65539]:
+        xs = _stream(g.standard_normal(n), f)
+        got = run_scal(n, -0.1234567890123, xs, f, 1, mode)
+        check_scal(got, n, -0.1234567890123, xs, f, 1, mode)
+
+
+def test_scal_config_mixture_and_paths():
+    """The 1M double mixture (specials included) at k = 3, 4, 5, and strided / offset streams."""
+    n = 1 << 20
+    for k in (3, 4, 5):
+        xs = oracle.pack(inputs.mixture_f64(n, 1601), 1, k)
+        for mode in MODES:
+            got = run_scal(n, 1.5, xs, (k, 1), 1, mode)
+            check_scal(got, n, 1.5, xs, (k, 1), 1, mode)
+    g = np.random.default_rng(21)
+    for f, inc, off in [((5, 1), 3, 0), ((4, 1), 1, 1), ((3, 0), 2, 7), ((2, 0), 1, 2)]:
+        m = 10007
+        xs = _stream(g.standard_normal(m * inc), f)
+        got = run_scal(m, 2.75, xs, f, inc, "rne", off)
+        check_scal(got, m, 2.75, xs, f, inc, "rne")
+    with pytest.raises(flyte.FlyteError):
+        flyte.scal(1.0, torch.zeros(16, dtype=torch.uint8, device="cuda"), (9, 1), n=2)

@@ -132,3 +132,44 @@ def test_gemm_4096_double_k5_sampled():
     rows = s.integers(0, M, 2048)
     cols = s.integers(0, N, 2048)
     check(got, M, N, K, f, A, K, B, N, 1.0, 0.0, None, rows, cols)
+
+
+# ---- C stored as flytes (the pack fused into the epilogue) ---------------------------------
+
+@pytest.mark.parametrize("f,kc", [((2, 0), 2), ((3, 0), 3), ((4, 0), 2), ((3, 0), 4), ((5, 1), 3), ((5, 1), 6),
+                                  ((4, 1), 8)])
+def test_gemm_packed_c(f, kc):
+    """C as a kc-byte stream: the pack of the native-C gemm (same C0 = unpack(C)) bit for bit,
+    and within the gemm bound plus one rounding to kc bytes against the oracle."""
+    m, n, kk = 200, 300, 333
+    k, base = f
+    fc = (kc, base)
+    g = np.random.default_rng(40 + kc)
+    A = _codes(g.uniform(-1, 1, m * kk), f)
+    B = _codes(g.uniform(-1, 1, kk * n), f)
+    ct = np.float32 if base == 0 else np.float64
+    Cq = oracle.pack(g.uniform(-1, 1, m * n).astype(ct), base, kc)
+    C0 = oracle.values(Cq, base, kc).reshape(m, n)
+    wsb = flyte.workspace_bytes("gemm", m, n, kk, f)
+    ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device="cuda")
+    Ad, Bd = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    for alpha, beta, mode in [(1.0, 0.0, "rne"), (-1.5, 0.25, "rtz"), (0.75, 1.0, "rto"), (0.0, -2.0, "rne"),
+                              (0.0, 0.0, "half_up")]:
+        Cd = torch.from_numpy(Cq.copy()).cuda()
+        flyte.gemm_packed_c_raw(m, n, kk, alpha, Ad, f, kk, Bd, f, n, beta, Cd, fc, n, mode, ws, ws.numel())
+        torch.cuda.synchronize()
+        got = Cd.cpu().numpy()
+        native = run_gemm(m, n, kk, f, A, kk, B, n, alpha=alpha, beta=beta, C0=C0)
+        same = flyte.pack(torch.from_numpy(np.ascontiguousarray(native).reshape(-1).astype(ct)).cuda(), kc,
+                          mode).cpu().numpy()
+        assert np.array_equal(got, same), f"{np.sum(got != same)} bytes differ from pack(gemm)"
+        if alpha != 0.0:
+            v = oracle.values(got, base, kc).reshape(m, n)
+            mbits = (8 * kc - 9) if base == 0 else (8 * kc - 12)
+            rr, cc = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+            rows, cols = rr.reshape(-1), cc.reshape(-1)
+            ref, absum = oracle.gemm_entries(rows, cols, kk, alpha, A, (base, k), kk, B, (base, k), n, beta,
+                                             C0[rows, cols])
+            mag = abs(alpha) * absum + abs(beta) * np.abs(C0[rows, cols])
+            bound = (2.0 ** -22 if base == 0 else 4 * kk * 2.0 ** -53) * mag + np.abs(ref) * 2.0 ** -min(mbits, 52)
+            assert np.all(np.abs(v[rows, cols] - ref) <= bound + 2.0 ** -52 * np.abs(ref))

@@ -100,7 +100,7 @@ def test_gemv_parity_moderate(fa, trans, shape):
 @pytest.mark.parametrize("trans", ["N", "T"])
 @pytest.mark.parametrize("shape", [(1, 1), (3, 7), (5, 300), (300, 5), (257, 1029), (64, 4099),
                                    (1030, 64), (4099, 37), (2500, 2500), (2500, 2560), (3000, 9000),
-                                   (16, 12288)])
+                                   (16, 12288), (1027, 2048), (131, 1040)])
 def test_gemv_shapes_and_tails(trans, shape):
     m, n = shape
     fa = (5, 1)
@@ -117,9 +117,10 @@ def test_gemv_shapes_and_tails(trans, shape):
 
 @pytest.mark.parametrize("trans", ["N", "T"])
 @pytest.mark.parametrize("kind", ["positive", "wide"])
-def test_gemv_adversarial(trans, kind):
+@pytest.mark.parametrize("n", [2051, 2048])
+def test_gemv_adversarial(trans, kind, n):
     """All-positive terms (errors cannot cancel) and a 2^+-60 spread of magnitudes."""
-    m, n = 2600, 2051
+    m = 2600
     fa = (4, 1)
     A = make_A(m, n, fa, seed=5, kind=kind)
     x = np.abs(np.random.default_rng(6).standard_normal(max(m, n))) + 0.25
@@ -131,9 +132,10 @@ def test_gemv_adversarial(trans, kind):
 
 
 @pytest.mark.parametrize("trans", ["N", "T"])
-def test_gemv_specials_and_zeros(trans):
+@pytest.mark.parametrize("n", [1030, 1040])
+def test_gemv_specials_and_zeros(trans, n):
     """Zeros, subnormals, Inf and NaN in A, and Inf in x, take the binary64 path."""
-    m, n = 2100, 1030
+    m = 2101
     fa = (6, 1)
     g = np.random.default_rng(8)
     v = g.standard_normal(m * n)
@@ -247,3 +249,56 @@ def test_gemv_full_size_sampled(big_A, k):
                                      y0[cols], 1)
             check_bound(got[cols], ref, absum, 1.5, -0.5, y0[cols], m)
     del codes
+
+
+# ---- y stored as double-based flytes (the pack fused into the epilogue) -------------------
+
+def run_gemv_packed(trans, m, n, fa, Acodes, lda, x, ycodes, fy, alpha, beta, mode, incy=1):
+    buf = _dev(Acodes)
+    xd = _dev(x)
+    yd = _dev(ycodes.copy())
+    wsb = flyte.workspace_bytes("gemv_n" if trans == "N" else "gemv_t", m, n, 0, fa)
+    ws = torch.full((max(wsb, 16),), 0x55, dtype=torch.uint8, device="cuda")
+    flyte.gemv_packed_y_raw(trans, m, n, alpha, buf, fa, lda, xd, 1, beta, yd, fy, incy, mode, ws, ws.numel())
+    sync()
+    return yd.cpu().numpy()
+
+
+@pytest.mark.parametrize("trans", ["N", "T"])
+@pytest.mark.parametrize("ky", [2, 3, 5, 7, 8])
+@pytest.mark.parametrize("shape", [(777, 1283), (2100, 1024), (64, 9000)])
+def test_gemv_packed_y(trans, ky, shape):
+    """y as a ky-byte stream: equals the GPU's own pack of the binary64 gemv result bit for bit,
+    and meets the gemv bound plus one rounding to ky bytes against the oracle."""
+    m, n = shape
+    fa = (4, 1)
+    fy = (ky, 1)
+    A = make_A(m, n, fa, seed=11 + ky)
+    g = np.random.default_rng(23 + ky)
+    ly = m if trans == "N" else n
+    x = g.standard_normal(max(m, n))
+    ycodes = oracle.pack(g.standard_normal(ly), 1, ky)
+    yq = oracle.values(ycodes, 1, ky)                      # the values the codes stand for
+    for alpha, beta, mode in [(1.5, -0.5, "rne"), (-0.75, 0.0, "rtz"), (1.0, 1.0, "rto"),
+                              (0.0, 2.0, "rne"), (0.0, 0.0, "half_up")]:
+        got = run_gemv_packed(trans, m, n, fa, A, n, x, ycodes, fy, alpha, beta, mode)
+        # self-consistency on the GPU: pack(flyte_gemv(.., unpack(y), ..)) with the library's own pack
+        y64 = run_gemv(trans, m, n, fa, A, n, x, yq, alpha, beta)[:ly]
+        same = flyte.pack(torch.from_numpy(y64).cuda(), ky, mode).cpu().numpy()
+        assert np.array_equal(got, same), f"{np.sum(got != same)} bytes differ from pack(gemv)"
+        # against the oracle: the binary64 bound plus one rounding to ky bytes
+        ref, absum = reference(trans, m, n, fa, A, n, x, yq, alpha, beta)
+        v = oracle.values(got, 1, ky)
+        mag = abs(alpha) * absum + abs(beta) * np.abs(yq)
+        L = n if trans == "N" else m
+        bound = 4 * (L + 2) * EPS * mag + 2 * EPS * np.abs(ref) + np.abs(ref) * 2.0 ** -(8 * ky - 12)
+        assert np.all(np.abs(v - ref[:ly]) <= bound), "packed y out of bound"
+
+
+def test_gemv_packed_y_rejects_float_base():
+    A = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    x = torch.zeros(8, dtype=torch.float64, device="cuda")
+    y = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    with pytest.raises(flyte.FlyteError) as e:
+        flyte.gemv_packed_y_raw("N", 4, 4, 1.0, A, (4, 1), 4, x, 1, 0.0, y, (3, 0), 1, "rne", A, 64)
+    assert e.value.status == 2

@@ -303,6 +303,44 @@ def test_axpy_exact(base, kx, ky, mode):
         assert int(out[i]) == want
 
 
+@pytest.mark.parametrize("base,k", [(1, 3), (1, 5), (1, 7), (1, 8), (0, 2), (0, 3), (0, 4)])
+@pytest.mark.parametrize("mode", ["rne", "rtz", "rto"])
+def test_scal_exact(base, k, mode):
+    """scal against the exact rational product rounded once to the native type, then packed."""
+    n = 300
+    g = np.random.default_rng(500 + 10 * k + base)
+    alpha = -0.1234567890123 if base == 1 else 0.37
+    dt = np.float32 if base == 0 else np.float64
+    xs = oracle.pack(g.standard_normal(n).astype(dt), base, k)
+    out = _codes_from_stream(oracle.scal(n, alpha, xs, (base, k), 1, MODES[mode]), k)
+    xq = [exact.native_value(base, int(b)) for b in oracle.unpack(xs, base, k)]
+    a = Fraction(alpha) if base == 1 else Fraction(float(np.float32(alpha)))
+    for i in range(n):
+        ub = exact.round_to_native(base, a * xq[i])
+        ri = exact.native_value(base, ub)
+        if ri == 0:
+            continue
+        want = exact.round_to_code(base, k, ri, ri < 0, mode) if k < (4 if base == 0 else 8) else ub
+        assert int(out[i]) == want
+
+
+def test_scal_special_factors():
+    """alpha = 1 leaves codes unchanged, -1 flips the sign bit, 2 raises the exponent by one."""
+    k, base = 5, 1
+    v = np.random.default_rng(9).standard_normal(257)
+    xs = oracle.pack(v, base, k)
+    q = _codes_from_stream(xs, k).astype(np.uint64)
+    assert np.array_equal(oracle.scal(257, 1.0, xs, (base, k)), xs)
+    q_neg = _codes_from_stream(oracle.scal(257, -1.0, xs, (base, k)), k).astype(np.uint64)
+    assert np.array_equal(q_neg, q ^ np.uint64(1 << (8 * k - 1)))
+    q_two = _codes_from_stream(oracle.scal(257, 2.0, xs, (base, k)), k).astype(np.uint64)
+    assert np.array_equal(q_two, q + np.uint64(1 << (8 * k - 12)))   # exponent field starts at bit 8k - 12
+    # strided: untouched elements keep their bytes
+    out = oracle.scal(100, 2.0, xs, (base, k), incx=2)
+    qs = _codes_from_stream(out, k).astype(np.uint64)
+    assert np.array_equal(qs[1:200:2], q[1:200:2]) and np.array_equal(qs[0:200:2], q[0:200:2] + np.uint64(1 << (8 * k - 12)))
+
+
 def test_gemv_exact_small():
     g = np.random.default_rng(41)
     for (m, n) in [(1, 1), (3, 5), (9, 4), (17, 23)]:
