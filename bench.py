@@ -56,7 +56,54 @@ def parse_args():
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=6144, help="rows of the CPU-baseline sample")
+    ap.add_argument("--case", choices=["gemv", "convert", "blas1", "gemm"],
+                    help="run one small invocation of these kernels (for profilers) and exit; no JSON line")
+    ap.add_argument("--k", type=int, default=6, help="byte width for --case")
+    ap.add_argument("--size", type=int, default=8192, help="matrix side (gemv, gemm) for --case")
     return ap.parse_args()
+
+
+def run_case(args):
+    """One call of the kernels of a hot-path row on a small, seeded case (inputs larger than L2 but a few
+    GB at most), with one untimed call before it; used to capture hardware counters."""
+    import torch
+
+    from paper_1601_07789_gb300 import flyte
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2)
+    k, size = args.k, args.size
+    if args.case == "gemv":
+        codes = flyte.pack(torch.randn(size * size, dtype=torch.float64, device=dev, generator=gen), k)
+        x = torch.randn(size, dtype=torch.float64, device=dev, generator=gen)
+        y = torch.randn(size, dtype=torch.float64, device=dev, generator=gen)
+        for _ in range(2):
+            for t in "NT":
+                flyte.gemv(t, size, size, ALPHA, codes, (k, 1), size, x, BETA, y)
+    elif args.case == "convert":
+        n = 1 << 26
+        v = torch.randn(n, dtype=torch.float64, device=dev, generator=gen)
+        c = torch.empty(n * k, dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            flyte.pack(v, k, out=c)
+            flyte.unpack(c, k, flyte.F64, out=v)
+    elif args.case == "blas1":
+        n = 1 << 26
+        xs = flyte.pack(torch.randn(n, dtype=torch.float64, device=dev, generator=gen), k)
+        ys = flyte.pack(torch.randn(n, dtype=torch.float64, device=dev, generator=gen), k)
+        for _ in range(2):
+            flyte.dot(xs, (k, 1), ys, (k, 1))
+            flyte.axpy(1e-9, xs, (k, 1), ys, (k, 1))
+    elif args.case == "gemm":
+        base = 0 if k <= 4 else 1
+        dt = torch.float32 if base == 0 else torch.float64
+        A = flyte.pack(torch.rand(size * size, dtype=dt, device=dev, generator=gen) * 2 - 1, k)
+        B = flyte.pack(torch.rand(size * size, dtype=dt, device=dev, generator=gen) * 2 - 1, k)
+        C = torch.empty(size * size, dtype=dt, device=dev)
+        for _ in range(2):
+            flyte.gemm(size, size, size, A, (k, base), B, (k, base), C=C)
+    torch.cuda.synchronize()
 
 
 def gemv_bytes(k: int, trans: str) -> int:
@@ -277,7 +324,8 @@ def run_flyte(args):
                    y if yv is None else yv, ws=ws[trans])
 
     calls = [(k, t) for k in KS for t in "NT"]
-    launches_per_step = sum(2 if t == "N" else 3 for _, t in calls)
+    # each call: the x split, the main kernel and the partial-sum epilogue (16384 columns are 4 'N' tiles)
+    launches_per_step = 3 * len(calls)
 
     for _ in range(args.warmup):
         for k, t in calls:
@@ -352,7 +400,7 @@ def run_flyte(args):
             }
     hbm_peak, peak_kind = load_peaks()
     dom = max(calls, key=lambda c: per_call_ms[c])
-    dom_key = f"gemv_{dom[1].lower()}_kernel<F64,{dom[0]}>"
+    dom_key = f"gemv_n_pc<F64,{dom[0]}>" if dom[1] == "N" else f"gemv_t_kernel<F64,{dom[0]}>"
     achieved = gemv_bytes(*dom) / (per_call_ms[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom_key, "achieved": round(achieved, 1), "peak": hbm_peak,
                 "peak_kind": f"of {peak_kind}", "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
@@ -488,6 +536,7 @@ def run_rows(dev, hbm_peak):
     rows["n"] = n
     del v, out, xs, ys
     rows.update(run_gemm_rows(dev))
+    rows.update(run_refine_rows(dev))
     return rows
 
 
@@ -545,9 +594,48 @@ def run_gemm_rows(dev):
     return out
 
 
+def run_refine_rows(dev):
+    """Refinement rows: n = 8192, A = G/sqrt(n) + n I, b N(0,1), to 1e-12 relative residual with two
+    Jacobi sweeps per correction on A stored at k = 3, 4, 5, against the same solver with the binary64
+    matrix (k = 8) in the sweeps (the native-FP64 baseline)."""
+    import torch
+
+    from paper_1601_07789_gb300 import flyte
+    n = 8192
+    stream = torch.cuda.current_stream()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(8)
+    A = torch.randn(n, n, dtype=torch.float64, device=dev, generator=gen) / n ** 0.5
+    A.diagonal().add_(float(n))
+    gen.manual_seed(9)
+    b = torch.randn(n, dtype=torch.float64, device=dev, generator=gen)
+    A = A.reshape(-1)
+    ws = torch.empty(flyte.workspace_bytes("refine", n, n, 0, (4, 1)), dtype=torch.uint8, device=dev)
+    out = {}
+    for k in (3, 4, 5, 8):
+        Ak = flyte.pack(A, k) if k < 8 else A.view(torch.uint8)
+        best = None
+        for _ in range(4):
+            x = torch.zeros(n, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it, rel = flyte.refine_jacobi(A, Ak, (k, 1), b, x, 1e-12, 50, 2, ws=ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        key = f"refine_n{n}_k{k}" if k < 8 else f"refine_n{n}_native_fp64"
+        out[key] = {"ms_to_solution": round(best, 3), "corrections": it, "relres": rel}
+    return out
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_flyte(args)

@@ -199,10 +199,30 @@ flyte_status flyte_gemm_packed_c(int64_t m, int64_t n, int64_t k_, double alpha,
                                  flyte_fmt fc, int64_t ldc, flyte_round mode, void* ws, size_t ws_bytes,
                                  cudaStream_t stream);
 
+/* ---- mixed-precision iterative refinement ------------------------------------ */
+
+/* Solve A x = b (n x n, row-major) for a diagonally dominant A, keeping A
+ * twice: A64 in binary64 (lda64) for the residual and Ak, the same matrix as
+ * k-byte flytes (fa, lda), for the correction sweeps -- the paper's premise
+ * (Sec. 1-2) that storage precision can follow what the algorithm needs.
+ *   repeat:  r = b - A64 x  (flyte_gemv with k = 8);  stop if ||r||_2 <= tol ||b||_2
+ *            or after max_outer corrections;
+ *            d = 0; `inner` times: d <- d + D^-1 (r - Ak d)  (Jacobi-Richardson,
+ *            flyte_gemv on Ak; D = diag(A64));  x <- x + d
+ * x: device vector, the initial guess on entry, the solution on return.
+ * ws: flyte_workspace_bytes("refine", n, n, 0, fa) bytes, 256-byte aligned.
+ * *iters (may be NULL): corrections applied; *relres (may be NULL): the last
+ * ||r||_2 / ||b||_2.  Unlike the other entry points this call is synchronous:
+ * it reads one norm back to the host per outer iteration (stream s). */
+flyte_status flyte_refine_jacobi(int64_t n, const double* A64, int64_t lda64, const void* Ak, flyte_fmt fa,
+                                 int64_t lda, const double* b, double* x, double tol, int max_outer, int inner,
+                                 void* ws, size_t ws_bytes, cudaStream_t stream, int* iters, double* relres);
+
 /* ---- helpers ---------------------------------------------------------------- */
 
 /* Scratch bytes an operation needs for the given sizes: op is "dot",
- * "gemv_n", "gemv_t" or "gemm" (m, n, k_ as in that call; unused ones 0).
+ * "gemv_n", "gemv_t", "gemm" or "refine" (m, n, k_ as in that call; unused
+ * ones 0).
  * Returns 0 for an operation that needs none and (size_t)-1 for an unknown
  * op.  The amount depends only on the arguments, never on the device. */
 size_t flyte_workspace_bytes(const char* op, int64_t m, int64_t n, int64_t k_, flyte_fmt f);

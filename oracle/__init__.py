@@ -72,6 +72,9 @@ def lib() -> ctypes.CDLL:
             L.orc_axpy.restype = i32
             L.orc_scal.argtypes = [i64, dbl, vp, i32, i32, i64, i32]
             L.orc_scal.restype = i32
+            L.orc_refine_jacobi.argtypes = [i64, vp, i64, vp, i32, i32, i64, vp, vp, dbl, i32, i32,
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+            L.orc_refine_jacobi.restype = i32
             L.orc_gemv.argtypes = [ctypes.c_char, i64, i64, dbl, vp, i32, i32, i64, vp, i64, dbl,
                                    vp, i64, vp]
             L.orc_gemv.restype = i32
@@ -183,6 +186,20 @@ def gemv(trans: str, m: int, n: int, alpha: float, A: np.ndarray, fa: tuple[int,
     _check(lib().orc_gemv(trans.encode(), m, n, alpha, _ptr(A), fa[0], fa[1], lda, _ptr(x), incx,
                           beta, _ptr(y), incy, _ptr(absum)), "gemv")
     return y, absum[:leny]
+
+
+def refine_jacobi(n: int, A64: np.ndarray, Ak: np.ndarray, fa: tuple[int, int], b: np.ndarray, x0: np.ndarray,
+                  tol: float, max_outer: int, inner: int):
+    """Return (x, corrections, relres) of the refinement solve (A64: binary64 values, Ak: k-byte codes)."""
+    A64 = np.ascontiguousarray(A64, dtype=np.float64).view(np.uint8)
+    Ak = np.ascontiguousarray(Ak, dtype=np.uint8)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.array(x0, dtype=np.float64, copy=True)
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    _check(lib().orc_refine_jacobi(n, _ptr(A64), n, _ptr(Ak), fa[0], fa[1], n, _ptr(b), _ptr(x), tol,
+                                   max_outer, inner, ctypes.byref(it), ctypes.byref(rel)), "refine_jacobi")
+    return x, it.value, rel.value
 
 
 def gemm_entries(rows: np.ndarray, cols: np.ndarray, kk: int, alpha: float, A: np.ndarray,

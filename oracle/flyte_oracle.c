@@ -389,6 +389,54 @@ int orc_gemv(char trans, int64_t m, int64_t n, double alpha, const uint8_t *A, i
     return 0;
 }
 
+/* ---- mixed-precision iterative refinement ------------------------------- */
+
+/* Solve A x = b with the residual on the binary64 matrix A64 (read as k = 8
+ * double-based codes) and Jacobi-Richardson correction sweeps on the k-byte
+ * copy Ak, in the order of the library's description:
+ *   r = b - A64 x; stop if ||r|| <= tol ||b|| or after max_outer corrections;
+ *   d = 0; inner times: d = d + (r - Ak d) / diag(A64); x = x + d.
+ * Products use orc_gemv (Dot2); norms are plain binary64 sums of squares.
+ * x holds the initial guess and receives the result. */
+int orc_refine_jacobi(int64_t n, const uint8_t *A64, int64_t lda64, const uint8_t *Ak, int base, int k,
+                      int64_t lda, const double *b, double *x, double tol, int max_outer, int inner,
+                      int *iters, double *relres)
+{
+    if (!orc_valid(base, k) || n < 0 || lda64 < n || lda < n || max_outer < 0 || inner < 1) return -1;
+    double *r = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *t = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *d = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *diag = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!r || !t || !d || !diag) { free(r); free(t); free(d); free(diag); return -1; }
+    double bb = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        bb += b[i] * b[i];
+        diag[i] = code_value(1, 8, A64 + (size_t)(i * lda64 + i) * 8u);
+    }
+    const double bnorm = sqrt(bb);
+    int it = 0;
+    double rel = 0.0;
+    for (;; ++it) {
+        memcpy(r, b, sizeof(double) * (size_t)n);
+        orc_gemv('N', n, n, -1.0, A64, 1, 8, lda64, x, 1, 1.0, r, 1, NULL);
+        double rr = 0.0;
+        for (int64_t i = 0; i < n; ++i) rr += r[i] * r[i];
+        rel = bnorm > 0.0 ? sqrt(rr) / bnorm : sqrt(rr);
+        if (!(rel > tol) || it >= max_outer) break;
+        for (int64_t i = 0; i < n; ++i) d[i] = 0.0;
+        for (int j = 0; j < inner; ++j) {
+            memcpy(t, r, sizeof(double) * (size_t)n);
+            if (j > 0) orc_gemv('N', n, n, -1.0, Ak, base, k, lda, d, 1, 1.0, t, 1, NULL);
+            for (int64_t i = 0; i < n; ++i) d[i] = d[i] + t[i] / diag[i];
+        }
+        for (int64_t i = 0; i < n; ++i) x[i] += d[i];
+    }
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    free(r); free(t); free(d); free(diag);
+    return 0;
+}
+
 /* ---- gemm (BLAS level 3, Sec. 6.3.3) ------------------------------------ */
 
 /* C_ij for the listed (i, j) pairs of row-major C = alpha*A*B + beta*C0, with

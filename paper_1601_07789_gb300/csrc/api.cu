@@ -208,6 +208,25 @@ flyte_status flyte_gemm_packed_c(int64_t m, int64_t n, int64_t k_, double alpha,
   return launch_gemm(m, n, k_, alpha, A, fa, lda, B, ldb, beta, C, kc, ldc, int(mode), ws, ws_bytes, stream);
 }
 
+flyte_status flyte_refine_jacobi(int64_t n, const double* A64, int64_t lda64, const void* Ak, flyte_fmt fa,
+                                 int64_t lda, const double* b, double* x, double tol, int max_outer, int inner,
+                                 void* ws, size_t ws_bytes, cudaStream_t stream, int* iters, double* relres) {
+  g_error[0] = 0;
+  if (!valid_fmt(fa)) return invalid("format (k, base)");
+  if (n < 0) return invalid("n < 0");
+  if (lda64 < (n > 1 ? n : 1) || lda < (n > 1 ? n : 1)) return invalid("leading dimension");
+  if (max_outer < 0 || inner < 1) return invalid("max_outer < 0 or inner < 1");
+  if (!(tol >= 0.0)) return invalid("tol");
+  if (n == 0) {
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return FLYTE_OK;
+  }
+  if (!A64 || !Ak || !b || !x) return invalid("null pointer");
+  return launch_refine(n, A64, lda64, Ak, fa, lda, b, x, tol, max_outer, inner, ws, ws_bytes, stream, iters,
+                       relres);
+}
+
 size_t flyte_workspace_bytes(const char* op, int64_t m, int64_t n, int64_t k_, flyte_fmt f) {
   (void)k_;
   if (!op || m < 0 || n < 0 || k_ < 0) return size_t(-1);
@@ -215,6 +234,7 @@ size_t flyte_workspace_bytes(const char* op, int64_t m, int64_t n, int64_t k_, f
   if (std::strcmp(op, "gemm") == 0) return gemm_workspace_bytes(m, n, k_, f);
   if (std::strcmp(op, "gemv_n") == 0) return gemv_workspace_bytes('N', m, n, f);
   if (std::strcmp(op, "gemv_t") == 0) return gemv_workspace_bytes('T', m, n, f);
+  if (std::strcmp(op, "refine") == 0) return refine_workspace_bytes(n);
   return size_t(-1);
 }
 

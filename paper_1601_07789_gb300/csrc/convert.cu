@@ -21,6 +21,14 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kUnroll = 4;
 
+// Bit k set: double-based width k uses the warp-tile kernels below.
+#ifndef FLYTE_PACK_TILES_MASK
+#define FLYTE_PACK_TILES_MASK 0x8E   // k = 1, 2, 3, 7 (k = 4..6 measured 2-3 % faster without)
+#endif
+#ifndef FLYTE_UNPACK_TILES_MASK
+#define FLYTE_UNPACK_TILES_MASK 0xFE
+#endif
+
 // 4 native values: 16 bytes (float) or 32 bytes (double).
 template <int BASE>
 struct Quad {
@@ -254,7 +262,7 @@ flyte_status launch_unpack(void* dst, const void* src, int64_t n, flyte_fmt f, i
     using Bits = typename Native<BASE>::bits;
     int64_t first = 0;
     const bool fast = inc_src == 1 && inc_dst == 1 && aligned(src, group_bytes(K)) && aligned(dst, 16);
-    if constexpr (BASE == FLYTE_F64 && K < 8) {
+    if constexpr (BASE == FLYTE_F64 && K < 8 && ((FLYTE_UNPACK_TILES_MASK >> K) & 1)) {
       if (fast && n >= 128) {
         const int64_t ntiles = n / 128;
         unpack_f64_tiles<K><<<grid_for(ntiles * 32, kThreads * kUnroll, 6), kThreads, 0, s>>>(
@@ -287,7 +295,7 @@ flyte_status launch_pack(void* dst, const void* src, int64_t n, flyte_fmt f, int
     int64_t first = 0;
     using Bits = typename Native<BASE>::bits;
     const bool fast = inc_src == 1 && inc_dst == 1 && aligned(src, 16) && aligned(dst, group_bytes(K));
-    if constexpr (BASE == FLYTE_F64 && K < 8) {
+    if constexpr (BASE == FLYTE_F64 && K < 8 && ((FLYTE_PACK_TILES_MASK >> K) & 1)) {
       if (fast && aligned(dst, 16) && n >= 128) {
         const int64_t ntiles = n / 128;
         pack_f64_tiles<K><<<grid_for(ntiles * 32, kThreads * kUnroll, 6), kThreads, 0, s>>>(

@@ -372,5 +372,9 @@ flyte_status launch_gemm(int64_t m, int64_t n, int64_t kdim, double alpha, const
                          int64_t lda, const void* B, int64_t ldb, double beta, void* C, int kc, int64_t ldc,
                          int mode, void* ws, size_t ws_bytes, cudaStream_t s);
 size_t gemm_workspace_bytes(int64_t m, int64_t n, int64_t kdim, flyte_fmt f);
+flyte_status launch_refine(int64_t n, const double* A64, int64_t lda64, const void* Ak, flyte_fmt fa, int64_t lda,
+                           const double* b, double* x, double tol, int max_outer, int inner, void* ws,
+                           size_t ws_bytes, cudaStream_t s, int* iters_out, double* relres_out);
+size_t refine_workspace_bytes(int64_t n);
 
 }  // namespace flyte

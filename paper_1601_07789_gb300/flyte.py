@@ -28,7 +28,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "l
 # every entry point declared in include/flyte.h
 EXPORTS = ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_scal", "flyte_gemv",
            "flyte_gemv_packed_y", "flyte_gemv_static", "flyte_gemm", "flyte_gemm_packed_c",
-           "flyte_workspace_bytes", "flyte_last_error_string", "flyte_version")
+           "flyte_refine_jacobi", "flyte_workspace_bytes", "flyte_last_error_string", "flyte_version")
 
 
 class FlyteError(RuntimeError):
@@ -81,9 +81,11 @@ def lib() -> ctypes.CDLL:
                                      vp, sz, vp]
             L.flyte_gemm_packed_c.argtypes = [i64, i64, i64, dbl, vp, Fmt, i64, vp, Fmt, i64, dbl, vp, Fmt,
                                               i64, i32, vp, sz, vp]
+            L.flyte_refine_jacobi.argtypes = [i64, vp, i64, vp, Fmt, i64, vp, vp, dbl, i32, i32, vp, sz, vp,
+                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
             for name in ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_scal",
                          "flyte_gemv", "flyte_gemv_packed_y", "flyte_gemv_static", "flyte_gemm",
-                         "flyte_gemm_packed_c"):
+                         "flyte_gemm_packed_c", "flyte_refine_jacobi"):
                 getattr(L, name).restype = i32
             L.flyte_workspace_bytes.argtypes = [ctypes.c_char_p, i64, i64, i64, Fmt]
             L.flyte_workspace_bytes.restype = sz
@@ -270,3 +272,22 @@ def gemm(m: int, n: int, k: int, A: torch.Tensor, fa, B: torch.Tensor, fb,
         ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device=A.device)
     gemm_raw(m, n, k, alpha, A, fa, lda, B, fb, ldb, beta, C, ldc, ws, ws.numel(), stream)
     return C
+
+
+def refine_jacobi(A64: torch.Tensor, Ak: torch.Tensor, fa, b: torch.Tensor, x: torch.Tensor, tol: float = 1e-12,
+                  max_outer: int = 50, inner: int = 2, lda64: int | None = None, lda: int | None = None,
+                  ws: torch.Tensor | None = None, stream=None) -> tuple[int, float]:
+    """Iterative refinement of A x = b in place on x (binary64 residual on A64, Jacobi sweeps on the
+    k-byte copy Ak); returns (corrections applied, final relative residual).  Synchronous."""
+    n = b.numel()
+    fa = fmt(fa)
+    lda64 = n if lda64 is None else lda64
+    lda = n if lda is None else lda
+    if ws is None:
+        ws = torch.empty(workspace_bytes("refine", n, n, 0, fa), dtype=torch.uint8, device=b.device)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    _check(lib().flyte_refine_jacobi(n, _ptr(A64), lda64, _ptr(Ak), fa, lda, _ptr(b), _ptr(x), float(tol),
+                                     int(max_outer), int(inner), _ptr(ws), ws.numel(), _stream(stream),
+                                     ctypes.byref(it), ctypes.byref(rr)))
+    return it.value, rr.value

@@ -174,3 +174,12 @@ def gemm_operands_f64(M: int, N: int, K: int, seed_a: int = 5, seed_b: int = 6):
     A = rng(seed_a).uniform(-1.0, 1.0, size=(M, K))
     B = rng(seed_b).uniform(-1.0, 1.0, size=(K, N))
     return A, B
+
+
+def refine_system(n: int, seed_g: int = 8, seed_b: int = 9):
+    """Diagonally dominant system of the refinement workload: A = G / sqrt(n) + n I with G N(0,1)
+    (row-major float64), and b N(0,1)."""
+    A = rng(seed_g).standard_normal((n, n)) / np.sqrt(n)
+    A[np.arange(n), np.arange(n)] += n
+    b = rng(seed_b).standard_normal(n)
+    return A, b

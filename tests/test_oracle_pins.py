@@ -429,3 +429,45 @@ def test_dot_and_gemv_special_value_classes():
     A = oracle.pack(np.array([1.0, np.inf, 3.0, 4.0]), *f)
     y, _ = oracle.gemv("N", 2, 2, 1.0, A, f, 2, np.array([1.0, 1.0]), 1, 0.0, np.zeros(2), 1)
     assert y[0] == np.inf and y[1] == 7.0
+
+
+# ---- mixed-precision iterative refinement ------------------------------------------
+
+def _dd_system(n, seed):
+    g = np.random.default_rng(seed)
+    A = g.standard_normal((n, n)) / np.sqrt(n) + n * np.eye(n)
+    return A, g.standard_normal(n)
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_refine_converges_to_the_solution(k):
+    """The refinement reaches the requested residual, and its x agrees with LAPACK's solve."""
+    n = 256
+    A, b = _dd_system(n, 70 + k)
+    Ak = oracle.pack(A.reshape(-1), 1, k)
+    x, it, rel = oracle.refine_jacobi(n, A, Ak, (1, k), b, np.zeros(n), 1e-12, 30, 2)
+    assert rel <= 1e-12 and 1 <= it <= 30
+    true_rel = np.linalg.norm(b - A @ x) / np.linalg.norm(b)     # residual recomputed by NumPy
+    assert true_rel <= 2e-12
+    xs = np.linalg.solve(A, b)
+    smin = np.linalg.svd(A, compute_uv=False)[-1]                # ||x - xs|| <= ||A^-1|| ||r||
+    assert np.linalg.norm(x - xs) <= 1.01 * np.linalg.norm(b - A @ x) / smin + 1e-15 * np.linalg.norm(xs)
+
+
+def test_refine_one_step_semantics():
+    """max_outer = 1 with one sweep is exactly x1 = x0 + D^-1 (b - A x0), written out in NumPy; with
+    tol = inf nothing is corrected; the contraction per correction follows the stored precision."""
+    n = 64
+    A, b = _dd_system(n, 7)
+    x0 = np.random.default_rng(8).standard_normal(n)
+    Ak = oracle.pack(A.reshape(-1), 1, 4)
+    x1, it, _ = oracle.refine_jacobi(n, A, Ak, (1, 4), b, x0, 0.0, 1, 1)
+    want = x0 + (b - A @ x0) / np.diag(A)
+    assert it == 1 and np.max(np.abs(x1 - want)) <= 1e-12 * np.max(np.abs(want))
+    x2, it2, rel2 = oracle.refine_jacobi(n, A, Ak, (1, 4), b, x0, np.inf, 10, 2)
+    assert it2 == 0 and np.array_equal(x2, x0)
+    assert abs(rel2 - np.linalg.norm(b - A @ x0) / np.linalg.norm(b)) <= 1e-12
+    # fewer stored bytes converge more slowly: k = 3 needs at least as many corrections as k = 5
+    its = [oracle.refine_jacobi(n, A, oracle.pack(A.reshape(-1), 1, k), (1, k), b, np.zeros(n), 1e-14, 30, 4)[1]
+           for k in (3, 5)]
+    assert its[0] >= its[1]
