@@ -537,6 +537,7 @@ def run_rows(dev, hbm_peak):
     del v, out, xs, ys
     rows.update(run_gemm_rows(dev))
     rows.update(run_refine_rows(dev))
+    rows.update(run_batch_rows(dev))
     return rows
 
 
@@ -629,6 +630,111 @@ def run_refine_rows(dev):
         key = f"refine_n{n}_k{k}" if k < 8 else f"refine_n{n}_native_fp64"
         out[key] = {"ms_to_solution": round(best, 3), "corrections": it, "relres": rel}
     return out
+
+
+def run_batch_rows(dev):
+    """Batched uneven jobs: 4096 jobs (unpack / dot / axpy with lengths log-uniform in 10^3..10^6,
+    gemv N / T with sides log-uniform in 64..4096; double-based k = 2..7 or float-based k = 2, 3) as one
+    persistent launch replayed from a CUDA graph, against one launch per job (eager, and the same
+    per-job launches captured in a CUDA graph).  Inputs are shared read-only pools per format."""
+    import torch
+
+    from paper_1601_07789_gb300 import flyte, inputs
+    stream = torch.cuda.current_stream()
+    specs = inputs.batch_specs(4096, seed=5)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(11)
+    pool_len = max(max(s["n"] * max(s["m"], 1) for s in specs), 1 << 20)
+    pools = {}
+    for k, base in inputs.BATCH_FORMATS:
+        dt = torch.float32 if base == 0 else torch.float64
+        pools[(k, base)] = flyte.pack(torch.randn(pool_len, dtype=dt, device=dev, generator=gen), k)
+    xpool = torch.randn(4096, dtype=torch.float64, device=dev, generator=gen)
+    jobs, calls, keep = [], [], []
+    total_bytes = 0
+    for s in specs:
+        op, k, base, n, m = s["op"], s["k"], s["base"], s["n"], s["m"]
+        f = (k, base)
+        W = 4 if base == 0 else 8
+        pool = pools[f]
+        if op == 0:
+            out = torch.empty(n, dtype=torch.float32 if base == 0 else torch.float64, device=dev)
+            keep.append(out)
+            jobs.append(flyte.job(flyte.JOB_UNPACK, f, n, pool, out))
+            calls.append(lambda n=n, f=f, out=out, pool=pool: flyte.unpack_raw(out, pool, n, f))
+            total_bytes += n * (k + W)
+        elif op == 1:
+            res = torch.empty((), dtype=torch.float64, device=dev)
+            wsd = torch.empty(flyte.workspace_bytes("dot", 0, n, 0, f), dtype=torch.uint8, device=dev)
+            keep += [res, wsd]
+            ysl = pool[k * (pool_len - n):]
+            jobs.append(flyte.job(flyte.JOB_DOT, f, n, pool, ysl, fy=f, result=res))
+            calls.append(lambda n=n, f=f, res=res, wsd=wsd, pool=pool, ysl=ysl:
+                         flyte.dot_raw(res, n, pool, f, 1, ysl, f, 1, wsd, wsd.numel()))
+            total_bytes += 2 * n * k
+        elif op == 2:
+            y = pool[: n * k].clone()
+            keep.append(y)
+            jobs.append(flyte.job(flyte.JOB_AXPY, f, n, pool, y, fy=f, alpha=1e-9))
+            calls.append(lambda n=n, f=f, y=y, pool=pool: flyte.axpy(1e-9, pool, f, y, f, n=n))
+            total_bytes += 3 * n * k
+        else:
+            trans = "N" if op == 3 else "T"
+            ly = m if op == 3 else n
+            lx = n if op == 3 else m
+            y = torch.zeros(ly, dtype=torch.float64, device=dev)
+            wsg = torch.empty(flyte.workspace_bytes("gemv_n" if op == 3 else "gemv_t", m, n, 0, f),
+                              dtype=torch.uint8, device=dev)
+            keep += [y, wsg]
+            jobs.append(flyte.job(flyte.JOB_GEMV_N if op == 3 else flyte.JOB_GEMV_T, f, n, pool, y, m=m, xv=xpool,
+                                  alpha=1.0, beta=0.0))
+            calls.append(lambda trans=trans, m=m, n=n, f=f, y=y, wsg=wsg, pool=pool:
+                         flyte.gemv_raw(trans, m, n, 1.0, pool, f, n, xpool, 1, 0.0, y, 1, wsg, wsg.numel()))
+            total_bytes += m * n * k + 8 * lx + 8 * ly
+    ws = flyte.batch_prepare(jobs, device=dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    g1 = torch.cuda.CUDAGraph()
+    s1 = torch.cuda.Stream()
+    with torch.cuda.graph(g1, stream=s1):
+        flyte.batch_launch(ws, stream=s1)
+    t_batch = timed(g1.replay, 5)
+
+    def per_job():
+        for c in calls:
+            c()
+    t_eager = timed(per_job, 2)
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=s1):
+        with torch.cuda.stream(s1):
+            per_job()
+    t_graph = timed(g2.replay, 3)
+    flyte.batch_autotune(device=dev)
+    ws = flyte.batch_prepare(jobs, ws=ws, device=dev)
+    g3 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g3, stream=s1):
+        flyte.batch_launch(ws, stream=s1)
+    t_tuned = timed(g3.replay, 5)
+    gb = total_bytes / 1e9
+    return {"batch_4096_jobs": {
+        "jobs": len(specs), "GB": round(gb, 3),
+        "persistent_graph_ms": round(t_batch, 3), "persistent_graph_GBps": round(gb / (t_batch * 1e-3), 1),
+        "persistent_graph_autotuned_ms": round(t_tuned, 3),
+        "persistent_graph_autotuned_GBps": round(gb / (t_tuned * 1e-3), 1),
+        "per_job_launches_ms": round(t_eager, 3), "per_job_launches_GBps": round(gb / (t_eager * 1e-3), 1),
+        "per_job_launches_graph_ms": round(t_graph, 3),
+        "per_job_launches_graph_GBps": round(gb / (t_graph * 1e-3), 1)}}
 
 
 def main():

@@ -70,7 +70,7 @@ typedef enum {
  * Valid: base FLYTE_F32 with k in 1..4, base FLYTE_F64 with k in 1..8
  * (Table 1 lists 16..32 and 40..64 bits; the other widths follow the same
  * "top k bytes" rule).  k = 4 (F32) and k = 8 (F64) are the native types. */
-typedef struct {
+typedef struct flyte_fmt {
   int32_t k;
   int32_t base; /* flyte_base */
 } flyte_fmt;
@@ -217,6 +217,63 @@ flyte_status flyte_gemm_packed_c(int64_t m, int64_t n, int64_t k_, double alpha,
 flyte_status flyte_refine_jacobi(int64_t n, const double* A64, int64_t lda64, const void* Ak, flyte_fmt fa,
                                  int64_t lda, const double* b, double* x, double tol, int max_outer, int inner,
                                  void* ws, size_t ws_bytes, cudaStream_t stream, int* iters, double* relres);
+
+/* ---- batches of uneven jobs in one persistent launch ------------------------ */
+
+/* Many small operations of mixed widths amortise launch latency when they
+ * run as the tiles of one persistent kernel (the GPU counterpart of the
+ * paper's unrolled loops over mixed data, Sec. 6).  A job is one of: */
+typedef enum {
+  FLYTE_JOB_UNPACK = 0, /* y[i] = unpack(x_i), i < n; y native (float/double per fx.base) */
+  FLYTE_JOB_DOT = 1,    /* *result = sum_i x_i y_i over two flyte streams (fx, fy), i < n */
+  FLYTE_JOB_AXPY = 2,   /* y_i <- pack(fma(alpha, x_i, y_i), mode), i < n (fx.base == fy.base) */
+  FLYTE_JOB_GEMV_N = 3, /* y <- alpha A x + beta y; A m x n k-byte (fx), lda = n; x, y binary64 */
+  FLYTE_JOB_GEMV_T = 4  /* y <- alpha A^T x + beta y; same A */
+} flyte_job_op;
+
+/* One job (88 bytes, host memory when handed to flyte_batch_prepare).  All
+ * strides are 1 and matrices are dense (lda = n).  Semantics, accuracy and
+ * quick returns are those of flyte_unpack / flyte_dot / flyte_axpy /
+ * flyte_gemv. */
+typedef struct flyte_job {
+  int32_t op;         /* flyte_job_op */
+  int32_t mode;       /* flyte_round (AXPY) */
+  flyte_fmt fx;       /* x stream (UNPACK, DOT, AXPY) or A (GEMV) */
+  flyte_fmt fy;       /* y stream (DOT, AXPY); unused otherwise */
+  int64_t m, n;       /* GEMV: A is m x n; others: n elements (m unused) */
+  const void* a;      /* UNPACK/DOT/AXPY: x stream; GEMV: A */
+  const double* xv;   /* GEMV: x (n entries for N, m for T) */
+  void* y;            /* UNPACK: output; DOT: y stream; AXPY: y stream (in/out); GEMV: y */
+  double* result;     /* DOT: one double in device memory */
+  double alpha, beta; /* AXPY: alpha; GEMV: alpha, beta */
+} flyte_job;
+
+/* Plan a batch: split every job into tiles (tile sizes per (operation, k,
+ * base) from the table that flyte_batch_autotune fills, or built-in
+ * defaults), and upload the job and tile tables into ws (device, 256-byte
+ * aligned, flyte_batch_workspace_bytes(jobs, njobs) bytes).  Validates every
+ * job first (FLYTE_ERR_INVALID_ARG / FLYTE_ERR_UNSUPPORTED naming the job).
+ * Synchronous: returns when the tables are on the device.  Not capturable in
+ * a CUDA graph; the launch below is. */
+flyte_status flyte_batch_prepare(const flyte_job* jobs, int32_t njobs, void* ws, size_t ws_bytes,
+                                 cudaStream_t stream);
+size_t flyte_batch_workspace_bytes(const flyte_job* jobs, int32_t njobs);
+
+/* Run a prepared batch: one persistent kernel (one block per resident slot)
+ * whose blocks take tiles from a counter in ws until none are left; a dot's
+ * partial sums are added in tile order by the block that finishes its last
+ * tile, so results are deterministic.  Asynchronous, allocates nothing and
+ * may be captured in a CUDA graph and replayed (ws must stay untouched
+ * between prepare and the last replay).  Jobs in one batch must not write
+ * memory that another job of the batch reads or writes. */
+flyte_status flyte_batch_launch(void* ws, cudaStream_t stream);
+
+/* Time the candidate tile sizes of each (operation, k, base) on synthetic
+ * jobs (scratch from ws_bytes of device memory at ws, at least
+ * flyte_batch_autotune_bytes()) and keep the fastest in the library's tile
+ * table, which later flyte_batch_prepare calls use.  Synchronous. */
+flyte_status flyte_batch_autotune(void* ws, size_t ws_bytes, cudaStream_t stream);
+size_t flyte_batch_autotune_bytes(void);
 
 /* ---- helpers ---------------------------------------------------------------- */
 

@@ -227,6 +227,29 @@ flyte_status flyte_refine_jacobi(int64_t n, const double* A64, int64_t lda64, co
                        relres);
 }
 
+flyte_status flyte_batch_prepare(const flyte_job* jobs, int32_t njobs, void* ws, size_t ws_bytes,
+                                 cudaStream_t stream) {
+  g_error[0] = 0;
+  return batch_prepare(jobs, njobs, ws, ws_bytes, stream);
+}
+
+size_t flyte_batch_workspace_bytes(const flyte_job* jobs, int32_t njobs) {
+  g_error[0] = 0;
+  return batch_workspace_bytes(jobs, njobs);
+}
+
+flyte_status flyte_batch_launch(void* ws, cudaStream_t stream) {
+  g_error[0] = 0;
+  return batch_launch(ws, stream);
+}
+
+flyte_status flyte_batch_autotune(void* ws, size_t ws_bytes, cudaStream_t stream) {
+  g_error[0] = 0;
+  return batch_autotune(ws, ws_bytes, stream);
+}
+
+size_t flyte_batch_autotune_bytes(void) { return batch_autotune_bytes(); }
+
 size_t flyte_workspace_bytes(const char* op, int64_t m, int64_t n, int64_t k_, flyte_fmt f) {
   (void)k_;
   if (!op || m < 0 || n < 0 || k_ < 0) return size_t(-1);

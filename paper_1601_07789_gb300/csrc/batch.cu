@@ -1,0 +1,754 @@
+// batch.cu -- many uneven jobs of mixed widths as the tiles of one persistent kernel.
+//
+// flyte_batch_prepare splits each job into tiles (a range of elements, a
+// block of gemv rows, or a block of gemv columns) and uploads a job table and
+// a tile table into the caller's workspace.  flyte_batch_launch starts one
+// persistent kernel of (SMs x resident blocks) blocks; each block repeatedly
+// takes the next tile from an atomic counter and runs it with all its
+// threads, so short and long jobs share the machine without a launch per
+// job.  A dot's tiles leave partial sums in the workspace; the block that
+// completes a dot's last tile adds them in tile order, so the result does not
+// depend on the schedule.  The last block to finish resets the counters, so
+// a launch is a single kernel and can be replayed from a CUDA graph.  The
+// kernel has no inter-block waits.
+//
+// The arithmetic is that of the single-job kernels: exact widening and
+// integer narrowing (flyte_internal.cuh), double-word accumulation for
+// in-window data when the host has proven the error bound for the job
+// (dwacc.cuh), binary64 FMAs otherwise.  gemv splits x into binary32 pairs
+// once per tile in shared memory, which caps the batch gemv sides at 4096.
+//
+// Tile sizes come from a per-(operation, base, k) table: built-in defaults,
+// replaced by the fastest candidates that flyte_batch_autotune measures.
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "dwacc.cuh"
+
+namespace flyte {
+namespace {
+
+constexpr int kBThreads = 256;
+constexpr int kBWarps = kBThreads / 32;
+constexpr int64_t kMaxSide = 4096;          // gemv: x (split) is staged in shared memory
+constexpr int kNOps = 5;
+
+struct Item {
+  int32_t job, tile;
+  int64_t begin, end;                         // elements, rows ('N') or columns ('T')
+};
+
+struct JobDev {
+  flyte_job j;
+  int64_t tiles, part_base;
+  int32_t fast;                               // dot/gemv: double-word path proven; unpack/axpy: group path
+  int32_t fold_rows;                          // gemv 'T'
+};
+
+struct Header {
+  int32_t njobs, nitems;
+  int64_t off_jobs, off_items, off_parts, off_done;
+  int32_t counter;   // next tile to take
+  int32_t exited;    // blocks that have finished
+};
+
+int64_t up256(int64_t b) { return (b + 255) & ~int64_t(255); }
+
+// ---- tile table ----------------------------------------------------------------------------
+
+// tile size per (op, base, k): elements (UNPACK, DOT, AXPY), rows (GEMV_N); 'T' tiles are 1024 columns
+std::mutex g_tune_mu;
+int64_t g_tile[kNOps][2][9];
+bool g_tile_init = false;
+
+int64_t default_tile(int op) {
+  switch (op) {
+    case FLYTE_JOB_UNPACK: return 65536;
+    case FLYTE_JOB_DOT: return 65536;
+    case FLYTE_JOB_AXPY: return 65536;
+    case FLYTE_JOB_GEMV_N: return 16;
+    default: return 1024;
+  }
+}
+
+int64_t tile_for(int op, flyte_fmt f) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (!g_tile_init) {
+    for (int o = 0; o < kNOps; ++o)
+      for (int b = 0; b < 2; ++b)
+        for (int k = 0; k < 9; ++k) g_tile[o][b][k] = default_tile(o);
+    g_tile_init = true;
+  }
+  return g_tile[op][f.base][f.k];
+}
+
+void set_tile(int op, flyte_fmt f, int64_t t) {
+  tile_for(op, f);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tile[op][f.base][f.k] = t;
+}
+
+// ---- device helpers -----------------------------------------------------------------------
+
+// f(BASE, K) for a format known at run time (block-uniform).
+template <typename F>
+__device__ __forceinline__ void with_fmt(flyte_fmt f, F&& fn) {
+  if (f.base == FLYTE_F64) {
+    switch (f.k) {
+      case 1: fn.template operator()<FLYTE_F64, 1>(); break;
+      case 2: fn.template operator()<FLYTE_F64, 2>(); break;
+      case 3: fn.template operator()<FLYTE_F64, 3>(); break;
+      case 4: fn.template operator()<FLYTE_F64, 4>(); break;
+      case 5: fn.template operator()<FLYTE_F64, 5>(); break;
+      case 6: fn.template operator()<FLYTE_F64, 6>(); break;
+      case 7: fn.template operator()<FLYTE_F64, 7>(); break;
+      default: fn.template operator()<FLYTE_F64, 8>(); break;
+    }
+  } else {
+    switch (f.k) {
+      case 1: fn.template operator()<FLYTE_F32, 1>(); break;
+      case 2: fn.template operator()<FLYTE_F32, 2>(); break;
+      case 3: fn.template operator()<FLYTE_F32, 3>(); break;
+      default: fn.template operator()<FLYTE_F32, 4>(); break;
+    }
+  }
+}
+
+template <int BASE>
+__device__ __forceinline__ double native_to_double(typename Native<BASE>::bits u) {
+  if constexpr (BASE == FLYTE_F64) {
+    return __longlong_as_double((long long)u);
+  } else {
+    return double(__uint_as_float(u));
+  }
+}
+
+// binary32 pieces of an element (see dbl_to_pair); false outside the window
+template <int BASE, int K>
+__device__ __forceinline__ bool pieces(typename Native<BASE>::bits u, float& hi, float& lo) {
+  if constexpr (BASE == FLYTE_F64) {
+    return dbl_to_pair<K>(uint32_t(u >> 32), uint32_t(u), hi, lo);
+  } else {
+    hi = __uint_as_float(u);
+    lo = 0.f;
+    return flt_in_window(u);
+  }
+}
+
+// ---- UNPACK -------------------------------------------------------------------------------
+
+template <int BASE, int K>
+__device__ void unpack_tile(const JobDev& jd, int64_t b, int64_t e) {
+  using Bits = typename Native<BASE>::bits;
+  const uint8_t* src = static_cast<const uint8_t*>(jd.j.a);
+  Bits* dst = static_cast<Bits*>(jd.j.y);
+  int64_t i0 = b;
+  if (jd.fast) {
+    // b is a multiple of 4; whole groups [b/4, e/4)
+    for (int64_t g = b / 4 + threadIdx.x; g < e / 4; g += kBThreads) {
+      uint32_t w[K];
+      load_group<K>(src + g * (4 * K), w);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[4 * g + q] = extract_widened<BASE, K>(w, q);
+    }
+    i0 = e / 4 * 4;
+  }
+  for (int64_t i = i0 + threadIdx.x; i < e; i += kBThreads) dst[i] = widen<BASE, K>(load_code_bytes<K>(src + i * K));
+}
+
+// ---- AXPY ---------------------------------------------------------------------------------
+
+template <int BASE, int K>
+__device__ __forceinline__ uint64_t axpy_elem(typename Native<BASE>::bits ux, typename Native<BASE>::bits uy,
+                                              double alpha, int mode) {
+  if constexpr (BASE == FLYTE_F64) {
+    const double r = fma(alpha, __longlong_as_double((long long)ux), __longlong_as_double((long long)uy));
+    return narrow<BASE, K>(uint64_t(__double_as_longlong(r)), mode);
+  } else {
+    const float r = __fmaf_rn(__double2float_rn(alpha), __uint_as_float(ux), __uint_as_float(uy));
+    return narrow<BASE, K>(__float_as_uint(r), mode);
+  }
+}
+
+// y has format (BASE, K); x has the same base and width kx (any)
+template <int BASE, int K>
+__device__ void axpy_tile(const JobDev& jd, int64_t b, int64_t e) {
+  using Bits = typename Native<BASE>::bits;
+  constexpr int W = Native<BASE>::W;
+  const uint8_t* X = static_cast<const uint8_t*>(jd.j.a);
+  uint8_t* Y = static_cast<uint8_t*>(jd.j.y);
+  const int kx = jd.j.fx.k;
+  int64_t i0 = b;
+  if (jd.fast) {
+    for (int64_t g = b / 4 + threadIdx.x; g < e / 4; g += kBThreads) {
+      uint32_t wx[K], wy[K], wo[K];
+      load_group<K>(X + g * (4 * K), wx);
+      load_group_rw<K>(Y + g * (4 * K), wy);
+#pragma unroll
+      for (int j = 0; j < K; ++j) wo[j] = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        deposit_code<K>(wo, q, axpy_elem<BASE, K>(extract_widened<BASE, K>(wx, q), extract_widened<BASE, K>(wy, q),
+                                                  jd.j.alpha, jd.j.mode));
+      store_group<K>(Y + g * (4 * K), wo);
+    }
+    i0 = e / 4 * 4;
+  }
+  for (int64_t i = i0 + threadIdx.x; i < e; i += kBThreads) {
+    const uint64_t qx = load_code_bytes_rt(X + i * kx, kx);
+    const Bits ux = kx * 8 == W ? Bits(qx) : Bits(qx << (W - 8 * kx));
+    uint8_t* py = Y + i * K;
+    store_code_bytes<K>(py, axpy_elem<BASE, K>(ux, widen<BASE, K>(load_code_bytes<K>(py)), jd.j.alpha, jd.j.mode));
+  }
+}
+
+// ---- DOT ----------------------------------------------------------------------------------
+
+// Partial sum of x_i y_i over [b, e) for equal formats (BASE, K); every thread returns its share.
+template <int BASE, int K>
+__device__ double dot_share(const JobDev& jd, int64_t b, int64_t e) {
+  const uint8_t* X = static_cast<const uint8_t*>(jd.j.a);
+  const uint8_t* Y = static_cast<const uint8_t*>(jd.j.y);
+  DW acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dw_zero(acc[q]);
+  double acc64 = 0.0;
+  int64_t i0 = b;
+  if (jd.fast) {
+    for (int64_t g = b / 4 + threadIdx.x; g < e / 4; g += kBThreads) {
+      uint32_t wx[K], wy[K];
+      load_group<K>(X + g * (4 * K), wx);
+      load_group<K>(Y + g * (4 * K), wy);
+      typename Native<BASE>::bits ux[4], uy[4];
+      bool ok = true;
+      float p[4], s[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        ux[q] = extract_widened<BASE, K>(wx, q);
+        uy[q] = extract_widened<BASE, K>(wy, q);
+        float xh, xl, yh, yl;
+        ok &= pieces<BASE, K>(ux[q], xh, xl);
+        ok &= pieces<BASE, K>(uy[q], yh, yl);
+        pair_times_pair(xh, xl, yh, yl, p[q], s[q]);
+      }
+      if (ok) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dw_add(acc[q], p[q], s[q]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc64 = fma(native_to_double<BASE>(ux[q]), native_to_double<BASE>(uy[q]), acc64);
+      }
+    }
+    i0 = e / 4 * 4;
+  }
+  for (int64_t i = i0 + threadIdx.x; i < e; i += kBThreads)
+    acc64 = fma(code_to_double<BASE, K>(load_code_bytes<K>(X + i * K)),
+                code_to_double<BASE, K>(load_code_bytes<K>(Y + i * K)), acc64);
+  double v = acc64;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v += dw_value(acc[q]);
+  return v;
+}
+
+// mixed formats: binary64 FMAs over the raw bytes
+__device__ double dot_share_generic(const JobDev& jd, int64_t b, int64_t e) {
+  const uint8_t* X = static_cast<const uint8_t*>(jd.j.a);
+  const uint8_t* Y = static_cast<const uint8_t*>(jd.j.y);
+  const flyte_fmt fx = jd.j.fx, fy = jd.j.fy;
+  double acc = 0.0;
+  for (int64_t i = b + threadIdx.x; i < e; i += kBThreads)
+    acc = fma(code_to_double_rt(load_code_bytes_rt(X + i * fx.k, fx.k), fx.k, fx.base),
+              code_to_double_rt(load_code_bytes_rt(Y + i * fy.k, fy.k), fy.k, fy.base), acc);
+  return acc;
+}
+
+// ---- GEMV ---------------------------------------------------------------------------------
+
+// x1 = RN32(x), x2 = RN32(x - x1) for x = 0 or 2^-40 <= |x| < 2^40; else x1 = NaN (marks the job's
+// tile for the binary64 path), as prep_x of the single-job gemv.
+__device__ void split_x(const double* __restrict__ x, int64_t len, float* x1, float* x2) {
+  for (int64_t j = threadIdx.x; j < len; j += kBThreads) {
+    const double v = x[j];
+    const double av = fabs(v);
+    const bool ok = v == 0.0 || (av >= 0x1p-40 && av < 0x1p40);
+    float a = __double2float_rn(v);
+    float c = __double2float_rn(v - double(a));
+    if (!ok) {
+      a = __uint_as_float(0x7FC00000u);
+      c = 0.f;
+    }
+    x1[j] = a;
+    x2[j] = c;
+  }
+}
+
+template <int BASE, int K>
+__device__ __forceinline__ void fold_elem(typename Native<BASE>::bits u, float x1, float x2, DW& acc, bool& ok) {
+  float hi, lo, p, e;
+  ok &= pieces<BASE, K>(u, hi, lo);
+  pair_times_x(hi, lo, x1, x2, p, e);
+  dw_add(acc, p, e);
+}
+
+__device__ __forceinline__ double gemv_epilogue(double t, double alpha, double beta, const double* yp) {
+  return beta == 0.0 ? alpha * t : fma(alpha, t, beta * *yp);
+}
+
+// Rows [r0, r1) of y <- alpha A x + beta y: warp w takes rows r0 + w, r0 + w + 8, ...
+template <int BASE, int K>
+__device__ void gemv_n_tile(const JobDev& jd, int64_t r0, int64_t r1, float* x1, float* x2) {
+  const int64_t n = jd.j.n;
+  const uint8_t* A = static_cast<const uint8_t*>(jd.j.a);
+  const double* x = jd.j.xv;
+  double* y = static_cast<double*>(jd.j.y);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (jd.fast) {
+    split_x(x, n, x1, x2);
+    __syncthreads();
+  }
+  for (int64_t r = r0 + warp; r < r1; r += kBWarps) {
+    const uint8_t* Ar = A + r * n * K;
+    double t = 0.0;
+    bool good = false;
+    if (jd.fast) {
+      DW acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dw_zero(acc[q]);
+      bool ok = true;
+      for (int64_t g = lane; g < n / 4; g += 32) {
+        uint32_t w[K];
+        load_group<K>(Ar + g * (4 * K), w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          fold_elem<BASE, K>(extract_widened<BASE, K>(w, q), x1[4 * g + q], x2[4 * g + q], acc[q], ok);
+      }
+      for (int64_t c = n / 4 * 4 + lane; c < n; c += 32)
+        fold_elem<BASE, K>(widen<BASE, K>(load_code_bytes<K>(Ar + c * K)), x1[c], x2[c], acc[0], ok);
+      const DW s = dw_warp_sum(dw_sum4(acc[0], acc[1], acc[2], acc[3]));
+      t = __shfl_sync(0xFFFFFFFFu, dw_value(s), 0);
+      good = __all_sync(0xFFFFFFFFu, ok) && isfinite(t);
+    }
+    if (!good) {
+      double s2 = 0.0;
+      for (int64_t c = lane; c < n; c += 32) s2 = fma(code_to_double<BASE, K>(load_code_bytes<K>(Ar + c * K)), x[c], s2);
+      t = warp_sum(s2);
+    }
+    if (lane == 0) y[r] = gemv_epilogue(t, jd.j.alpha, jd.j.beta, y + r);
+  }
+}
+
+// Columns [c0, c1) of y <- alpha A^T x + beta y: thread t owns columns c0 + 4t .. + 3 over all rows.
+template <int BASE, int K>
+__device__ void gemv_t_tile(const JobDev& jd, int64_t c0, int64_t c1, float* x1, float* x2) {
+  const int64_t m = jd.j.m, n = jd.j.n;
+  const uint8_t* A = static_cast<const uint8_t*>(jd.j.a);
+  const double* x = jd.j.xv;
+  double* y = static_cast<double*>(jd.j.y);
+  if (jd.fast) {
+    split_x(x, m, x1, x2);
+    __syncthreads();
+  }
+  const int64_t c = c0 + 4 * threadIdx.x;
+  if (c >= c1) return;
+  const int nc = int(min(int64_t(4), c1 - c));
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  bool ok = jd.fast && nc == 4 && ((n * K) % group_bytes(K)) == 0;
+  if (ok) {
+    DW acc[2][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dw_zero(acc[0][q]), dw_zero(acc[1][q]);
+    const uint8_t* colp = A + c * K;
+    int since = 0;
+    for (int64_t i = 0; i < m; ++i) {
+      uint32_t w[K];
+      load_group<K>(colp + i * n * K, w);
+      const float a1 = x1[i], a2 = x2[i];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) fold_elem<BASE, K>(extract_widened<BASE, K>(w, q), a1, a2, acc[i & 1][q], ok);
+      if (++since == jd.fold_rows) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          v[q] += dw_value(acc[0][q]) + dw_value(acc[1][q]);
+          dw_zero(acc[0][q]);
+          dw_zero(acc[1][q]);
+        }
+        since = 0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      v[q] += dw_value(acc[0][q]) + dw_value(acc[1][q]);
+      ok = ok && isfinite(v[q]);
+    }
+  }
+  if (!ok) {
+    for (int q = 0; q < nc; ++q) {
+      double s2 = 0.0;
+      for (int64_t i = 0; i < m; ++i) s2 = fma(code_to_double<BASE, K>(load_code_bytes<K>(A + (i * n + c + q) * K)), x[i], s2);
+      v[q] = s2;
+    }
+  }
+  for (int q = 0; q < nc; ++q) y[c + q] = gemv_epilogue(v[q], jd.j.alpha, jd.j.beta, y + c + q);
+}
+
+// ---- the persistent kernel ----------------------------------------------------------------
+
+__global__ void __launch_bounds__(kBThreads) batch_kernel(uint8_t* __restrict__ ws) {
+  extern __shared__ __align__(16) float xs[];   // x1, x2 of the current gemv tile
+  __shared__ int s_item;
+  __shared__ double s_red[kBWarps];
+  Header* h = reinterpret_cast<Header*>(ws);
+  const JobDev* jobs = reinterpret_cast<const JobDev*>(ws + h->off_jobs);
+  const Item* items = reinterpret_cast<const Item*>(ws + h->off_items);
+  double* parts = reinterpret_cast<double*>(ws + h->off_parts);
+  int* done = reinterpret_cast<int*>(ws + h->off_done);
+  const int nitems = h->nitems;
+  if (blockIdx.x == 0) {
+    // a dot of length 0 has no tile: its result is written here
+    for (int i = threadIdx.x; i < h->njobs; i += kBThreads)
+      if (jobs[i].j.op == FLYTE_JOB_DOT && jobs[i].tiles == 0) *jobs[i].j.result = 0.0;
+  }
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(&h->counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const Item item = items[it];
+    const JobDev& jd = jobs[item.job];
+    const int op = jd.j.op;
+    if (op == FLYTE_JOB_UNPACK) {
+      with_fmt(jd.j.fx, [&]<int B, int K>() { unpack_tile<B, K>(jd, item.begin, item.end); });
+    } else if (op == FLYTE_JOB_AXPY) {
+      with_fmt(jd.j.fy, [&]<int B, int K>() { axpy_tile<B, K>(jd, item.begin, item.end); });
+    } else if (op == FLYTE_JOB_DOT) {
+      double v = 0.0;
+      if (jd.j.fx.k == jd.j.fy.k && jd.j.fx.base == jd.j.fy.base) {
+        with_fmt(jd.j.fx, [&]<int B, int K>() { v = dot_share<B, K>(jd, item.begin, item.end); });
+      } else {
+        v = dot_share_generic(jd, item.begin, item.end);
+      }
+      v = block_sum(v, s_red);
+      if (threadIdx.x == 0) {
+        parts[jd.part_base + item.tile] = v;
+        __threadfence();
+        if (atomicAdd(&done[item.job], 1) == int(jd.tiles) - 1) {
+          __threadfence();
+          double s = 0.0;
+          for (int64_t t = 0; t < jd.tiles; ++t) s += __ldcg(&parts[jd.part_base + t]);
+          *jd.j.result = s;
+        }
+      }
+    } else if (op == FLYTE_JOB_GEMV_N) {
+      with_fmt(jd.j.fx, [&]<int B, int K>() { gemv_n_tile<B, K>(jd, item.begin, item.end, xs, xs + kMaxSide); });
+    } else {
+      with_fmt(jd.j.fx, [&]<int B, int K>() { gemv_t_tile<B, K>(jd, item.begin, item.end, xs, xs + kMaxSide); });
+    }
+    __syncthreads();   // shared x and s_red are reused by the next tile
+  }
+  // The last block to finish resets the counters for the next launch (every
+  // other block has taken its last tile and finished it by then).
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&h->exited, 1) == int(gridDim.x) - 1) {
+      for (int i = 0; i < h->njobs; ++i) done[i] = 0;
+      h->counter = 0;
+      __threadfence();
+      h->exited = 0;
+    }
+  }
+}
+
+constexpr int kBatchSmem = 2 * kMaxSide * 4;   // x1, x2
+
+// ---- planning -------------------------------------------------------------------------------
+
+bool aligned_to(const void* p, int b) { return reinterpret_cast<uintptr_t>(p) % b == 0; }
+
+struct Plan {
+  std::vector<JobDev> jobs;
+  std::vector<Item> items;
+  int64_t nparts = 0;
+  int64_t bytes = 0;
+  Header hdr{};
+};
+
+flyte_status check_job(const flyte_job& j, int idx) {
+  auto bad = [&](const char* what) {
+    set_error("batch job %d: %s", idx, what);
+    return FLYTE_ERR_INVALID_ARG;
+  };
+  if (j.op < FLYTE_JOB_UNPACK || j.op > FLYTE_JOB_GEMV_T) return bad("unknown op");
+  if (!valid_fmt(j.fx)) return bad("format fx");
+  if ((j.op == FLYTE_JOB_DOT || j.op == FLYTE_JOB_AXPY) && !valid_fmt(j.fy)) return bad("format fy");
+  if (j.n < 0 || ((j.op == FLYTE_JOB_GEMV_N || j.op == FLYTE_JOB_GEMV_T) && j.m < 0)) return bad("negative size");
+  if (j.op == FLYTE_JOB_AXPY) {
+    if (j.fx.base != j.fy.base) {
+      set_error("batch job %d: axpy x and y must share the base", idx);
+      return FLYTE_ERR_UNSUPPORTED;
+    }
+    if (j.mode < FLYTE_RNE || j.mode > FLYTE_RTO) return bad("rounding mode");
+  }
+  if (j.op == FLYTE_JOB_GEMV_N || j.op == FLYTE_JOB_GEMV_T) {
+    const int64_t lenx = j.op == FLYTE_JOB_GEMV_N ? j.n : j.m;
+    if (lenx > kMaxSide) {
+      set_error("batch job %d: gemv x longer than %lld (use flyte_gemv)", idx, (long long)kMaxSide);
+      return FLYTE_ERR_UNSUPPORTED;
+    }
+  }
+  const bool empty = j.n == 0 || ((j.op == FLYTE_JOB_GEMV_N || j.op == FLYTE_JOB_GEMV_T) && j.m == 0);
+  if (!empty && (!j.a || !j.y)) return bad("null pointer");
+  if (!empty && j.op == FLYTE_JOB_DOT && !j.result) return bad("null result");
+  if (!empty && (j.op == FLYTE_JOB_GEMV_N || j.op == FLYTE_JOB_GEMV_T) && !j.xv) return bad("null x");
+  return FLYTE_OK;
+}
+
+flyte_status make_plan(const flyte_job* jobs, int njobs, Plan& p) {
+  if (njobs < 0 || (njobs > 0 && !jobs)) {
+    set_error("batch: bad job list");
+    return FLYTE_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < njobs; ++i) {
+    const flyte_status st = check_job(jobs[i], i);
+    if (st != FLYTE_OK) return st;
+  }
+  p.jobs.resize(size_t(njobs));
+  for (int i = 0; i < njobs; ++i) {
+    const flyte_job& j = jobs[i];
+    JobDev& d = p.jobs[size_t(i)];
+    std::memset(&d, 0, sizeof(d));
+    d.j = j;
+    const int op = j.op;
+    const int64_t tile = tile_for(op, op == FLYTE_JOB_AXPY ? j.fy : j.fx);
+    auto add_items = [&](int64_t total, int64_t step) {
+      int32_t t = 0;
+      for (int64_t b = 0; b < total; b += step, ++t) p.items.push_back(Item{i, t, b, std::min(total, b + step)});
+      d.tiles = t;
+    };
+    if (op == FLYTE_JOB_GEMV_N || op == FLYTE_JOB_GEMV_T) {
+      if (j.m == 0 || j.n == 0) continue;
+      const int K = j.fx.k;
+      const bool al = aligned_to(j.a, group_bytes(K)) && (j.n * K) % group_bytes(K) == 0;
+      if (op == FLYTE_JOB_GEMV_N) {
+        // chains of n/128 + 1 terms per slot, double-word tree 2 + 5, one binary64 step
+        const int64_t L = j.n / 128 + 2;
+        d.fast = al && dw_bound_ok(j.n, L, 1, 14, 7) ? 1 : 0;
+        add_items(j.m, tile);
+      } else {
+        // parity chains of fold/2 + 1 terms folded into binary64 every fold rows
+        d.fast = 0;
+        d.fold_rows = 64;
+        for (int64_t f = 64; f >= 2 && al; f /= 2) {
+          if (dw_bound_ok(j.m, f / 2 + 1, 2 * (j.m / f) + 4, 14)) {
+            d.fast = 1;
+            d.fold_rows = int32_t(f);
+            break;
+          }
+        }
+        add_items(j.n, 4 * kBThreads);
+      }
+    } else {
+      if (j.n == 0) continue;
+      const int64_t step = (tile + 3) / 4 * 4;
+      if (op == FLYTE_JOB_UNPACK) {
+        d.fast = aligned_to(j.a, group_bytes(j.fx.k)) && aligned_to(j.y, j.fx.base == FLYTE_F64 ? 8 : 4);
+      } else if (op == FLYTE_JOB_AXPY) {
+        d.fast = j.fx.k == j.fy.k && aligned_to(j.a, group_bytes(j.fy.k)) && aligned_to(j.y, group_bytes(j.fy.k));
+      } else {
+        // per thread: 4 slots, (step / 4) / threads groups each; block sum (3 + 5 levels) and the tiles
+        const int64_t L = step / (4 * kBThreads) + 1;
+        const int64_t tiles = (j.n + step - 1) / step;
+        d.fast = j.fx.k == j.fy.k && j.fx.base == j.fy.base && aligned_to(j.a, group_bytes(j.fx.k)) &&
+                 aligned_to(j.y, group_bytes(j.fx.k)) && dw_bound_ok(j.n, L, 4 + 8 + tiles + 1, 20);
+      }
+      add_items(j.n, step);
+      if (op == FLYTE_JOB_DOT) {
+        d.part_base = p.nparts;
+        p.nparts += d.tiles;
+      }
+    }
+  }
+  p.hdr.njobs = njobs;
+  p.hdr.nitems = int32_t(p.items.size());
+  p.hdr.off_jobs = 256;
+  p.hdr.off_items = p.hdr.off_jobs + up256(int64_t(sizeof(JobDev)) * njobs);
+  p.hdr.off_parts = p.hdr.off_items + up256(int64_t(sizeof(Item)) * int64_t(p.items.size()));
+  p.hdr.off_done = p.hdr.off_parts + up256(8 * p.nparts);
+  p.bytes = p.hdr.off_done + up256(4 * int64_t(njobs));
+  return FLYTE_OK;
+}
+
+int batch_blocks() {
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    int v = 0;
+    cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, batch_kernel, kBThreads, kBatchSmem) != cudaSuccess) v = 1;
+    per_sm = v < 1 ? 1 : v;
+  }
+  return per_sm * sm_count();
+}
+
+}  // namespace
+
+size_t batch_workspace_bytes(const flyte_job* jobs, int njobs) {
+  Plan p;
+  if (make_plan(jobs, njobs, p) != FLYTE_OK) return size_t(-1);
+  return size_t(p.bytes);
+}
+
+flyte_status batch_prepare(const flyte_job* jobs, int njobs, void* ws, size_t ws_bytes, cudaStream_t s) {
+  Plan p;
+  const flyte_status st = make_plan(jobs, njobs, p);
+  if (st != FLYTE_OK) return st;
+  if (ws == nullptr || ws_bytes < size_t(p.bytes) || reinterpret_cast<uintptr_t>(ws) % 256 != 0) {
+    set_error("batch: workspace of %lld bytes (256-byte aligned) required", (long long)p.bytes);
+    return FLYTE_ERR_WORKSPACE;
+  }
+  // header, jobs and tiles; the dot partials need no initial value; done counters start at 0
+  std::vector<uint8_t> host(size_t(p.bytes), 0);
+  std::memcpy(host.data(), &p.hdr, sizeof(Header));
+  if (!p.jobs.empty()) std::memcpy(host.data() + p.hdr.off_jobs, p.jobs.data(), sizeof(JobDev) * p.jobs.size());
+  if (!p.items.empty()) std::memcpy(host.data() + p.hdr.off_items, p.items.data(), sizeof(Item) * p.items.size());
+  if (cudaMemcpyAsync(ws, host.data(), host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cuda_status(cudaGetLastError(), "batch");
+  return FLYTE_OK;
+}
+
+flyte_status batch_launch(void* ws, cudaStream_t s) {
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0) {
+    set_error("batch: workspace must be the prepared, 256-byte aligned buffer");
+    return FLYTE_ERR_WORKSPACE;
+  }
+  const int blocks = batch_blocks();
+  batch_kernel<<<blocks, kBThreads, kBatchSmem, s>>>(static_cast<uint8_t*>(ws));
+  FLYTE_TRY_LAUNCH("batch");
+  return FLYTE_OK;
+}
+
+// ---- autotuning ----------------------------------------------------------------------------
+
+namespace {
+
+// Codes of in-window values (|v| in [1, 2) with random sign and mantissa) so that the timed path is
+// the double-word one, as for typical data.
+__global__ void fill_codes(uint8_t* p, int64_t n, int k, int base, uint32_t seed) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    uint64_t r = uint64_t(i) * 0x9E3779B97F4A7C15ull + seed;
+    r ^= r >> 29;
+    r *= 0xBF58476D1CE4E5B9ull;
+    r ^= r >> 32;
+    const int bits = 8 * k;
+    const int ebits = base == FLYTE_F64 ? 11 : 8;
+    const uint64_t bias = base == FLYTE_F64 ? 1023 : 127;
+    uint64_t code;
+    if (bits > 1 + ebits) {
+      const int mbits = bits - 1 - ebits;
+      code = ((r >> 63) << (bits - 1)) | (bias << mbits) | (r & ((uint64_t(1) << mbits) - 1));
+    } else {
+      code = (r >> 63) << (bits - 1) | (bias >> (ebits + 1 - bits));   // k = 1: the exponent's top bits
+    }
+    for (int b = 0; b < k; ++b) p[i * k + b] = uint8_t(code >> (8 * b));
+  }
+}
+
+__global__ void fill_ones(double* p, int64_t n) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = 1.0 + 1e-3 * double(i % 97);
+}
+
+constexpr int64_t kTuneJobs = 16;
+constexpr int64_t kTuneLen = int64_t(1) << 18;   // elements per streaming job
+constexpr int64_t kTuneSide = 1024;               // gemv jobs: 1024 x 1024
+constexpr int64_t kTuneData = 2 * kTuneJobs * kTuneLen * 8 + kTuneJobs * kTuneLen * 8;   // x, y streams, outputs
+constexpr int64_t kTuneWs = int64_t(1) << 20;
+
+}  // namespace
+
+size_t batch_autotune_bytes() { return size_t(kTuneData + kTuneWs + 4096); }
+
+flyte_status batch_autotune(void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (ws == nullptr || ws_bytes < batch_autotune_bytes() || reinterpret_cast<uintptr_t>(ws) % 256 != 0) {
+    set_error("batch autotune: %zu bytes of 256-byte aligned scratch required", batch_autotune_bytes());
+    return FLYTE_ERR_WORKSPACE;
+  }
+  uint8_t* w8 = static_cast<uint8_t*>(ws);
+  uint8_t* xs = w8;                                        // x streams (or A), up to 8 bytes per element
+  uint8_t* ys = xs + kTuneJobs * kTuneLen * 8;             // y streams (or gemv x, y)
+  uint8_t* out = ys + kTuneJobs * kTuneLen * 8;            // unpack outputs, dot results
+  uint8_t* bws = out + kTuneJobs * kTuneLen * 8;           // batch workspace
+  const flyte_fmt fmts[12] = {{1, 1}, {2, 1}, {3, 1}, {4, 1}, {5, 1}, {6, 1}, {7, 1}, {8, 1},
+                              {1, 0}, {2, 0}, {3, 0}, {4, 0}};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return cuda_status(cudaGetLastError(), "batch autotune");
+  flyte_status result = FLYTE_OK;
+  for (int op : {FLYTE_JOB_UNPACK, FLYTE_JOB_DOT, FLYTE_JOB_AXPY, FLYTE_JOB_GEMV_N}) {
+    for (const flyte_fmt& f : fmts) {
+      const bool gemv = op == FLYTE_JOB_GEMV_N;
+      const int64_t len = gemv ? kTuneSide * kTuneSide : kTuneLen;
+      const int64_t njob = gemv ? (kTuneJobs * kTuneLen * 8) / (len * f.k) : kTuneJobs;
+      fill_codes<<<grid_for(njob * len, 256), 256, 0, s>>>(xs, njob * len, f.k, f.base, 11u);
+      fill_codes<<<grid_for(kTuneJobs * kTuneLen, 256), 256, 0, s>>>(ys, kTuneJobs * kTuneLen, f.k, f.base, 12u);
+      if (gemv) fill_ones<<<grid_for(kTuneJobs * kTuneLen, 256), 256, 0, s>>>(reinterpret_cast<double*>(ys),
+                                                                              kTuneJobs * kTuneLen);
+      std::vector<flyte_job> jobs(static_cast<size_t>(njob));
+      for (int64_t i = 0; i < njob; ++i) {
+        flyte_job& j = jobs[size_t(i)];
+        std::memset(&j, 0, sizeof(j));
+        j.op = op;
+        j.fx = f;
+        j.fy = f;
+        j.mode = FLYTE_RNE;
+        j.alpha = 1e-9;
+        j.beta = 0.0;
+        if (gemv) {
+          j.m = j.n = kTuneSide;
+          j.a = xs + i * len * f.k;
+          j.xv = reinterpret_cast<const double*>(ys);
+          j.y = out + i * kTuneSide * 8;
+        } else {
+          j.n = len;
+          j.a = xs + i * len * f.k;
+          j.y = op == FLYTE_JOB_UNPACK ? static_cast<void*>(out + i * len * 8) : static_cast<void*>(ys + i * len * f.k);
+          j.result = reinterpret_cast<double*>(out) + i;
+        }
+      }
+      const int64_t cands_stream[3] = {16384, 65536, 262144};
+      const int64_t cands_rows[3] = {8, 16, 32};
+      const int64_t* cands = gemv ? cands_rows : cands_stream;
+      int64_t best = cands[1];
+      float best_ms = 1e30f;
+      for (int c = 0; c < 3 && result == FLYTE_OK; ++c) {
+        set_tile(op, f, cands[c]);
+        if ((result = batch_prepare(jobs.data(), int(njob), bws, size_t(kTuneWs), s)) != FLYTE_OK) break;
+        if ((result = batch_launch(bws, s)) != FLYTE_OK) break;   // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r)
+          if ((result = batch_launch(bws, s)) != FLYTE_OK) break;
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          result = cuda_status(cudaGetLastError(), "batch autotune");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = cands[c];
+        }
+      }
+      set_tile(op, f, best);
+      if (result != FLYTE_OK) break;
+    }
+    if (result != FLYTE_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return result;
+}
+
+}  // namespace flyte

@@ -376,5 +376,10 @@ flyte_status launch_refine(int64_t n, const double* A64, int64_t lda64, const vo
                            const double* b, double* x, double tol, int max_outer, int inner, void* ws,
                            size_t ws_bytes, cudaStream_t s, int* iters_out, double* relres_out);
 size_t refine_workspace_bytes(int64_t n);
+size_t batch_workspace_bytes(const flyte_job* jobs, int njobs);
+flyte_status batch_prepare(const flyte_job* jobs, int njobs, void* ws, size_t ws_bytes, cudaStream_t s);
+flyte_status batch_launch(void* ws, cudaStream_t s);
+size_t batch_autotune_bytes();
+flyte_status batch_autotune(void* ws, size_t ws_bytes, cudaStream_t s);
 
 }  // namespace flyte

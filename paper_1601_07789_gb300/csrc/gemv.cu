@@ -651,7 +651,10 @@ __global__ void scale_y(double* __restrict__ y, int64_t len, int64_t incy, doubl
     y[j * incy] = beta == 0.0 ? 0.0 : beta * y[j * incy];
 }
 
-constexpr int64_t kTRowTile = 128;   // row tile of gemv T
+#ifndef FLYTE_T_ROW_TILE
+#define FLYTE_T_ROW_TILE 128
+#endif
+constexpr int64_t kTRowTile = FLYTE_T_ROW_TILE;   // row tile of gemv T
 
 int64_t align16(int64_t b) { return (b + 15) & ~int64_t(15); }
 

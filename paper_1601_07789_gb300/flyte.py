@@ -28,7 +28,9 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "l
 # every entry point declared in include/flyte.h
 EXPORTS = ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_scal", "flyte_gemv",
            "flyte_gemv_packed_y", "flyte_gemv_static", "flyte_gemm", "flyte_gemm_packed_c",
-           "flyte_refine_jacobi", "flyte_workspace_bytes", "flyte_last_error_string", "flyte_version")
+           "flyte_refine_jacobi", "flyte_batch_prepare", "flyte_batch_workspace_bytes", "flyte_batch_launch",
+           "flyte_batch_autotune", "flyte_batch_autotune_bytes", "flyte_workspace_bytes",
+           "flyte_last_error_string", "flyte_version")
 
 
 class FlyteError(RuntimeError):
@@ -42,6 +44,17 @@ class Fmt(ctypes.Structure):
 
     def __repr__(self):
         return f"Fmt(k={self.k}, base={'F32' if self.base == F32 else 'F64'})"
+
+
+class Job(ctypes.Structure):
+    """flyte_job: one job of a batch (see include/flyte.h)."""
+    _fields_ = [("op", ctypes.c_int32), ("mode", ctypes.c_int32), ("fx", Fmt), ("fy", Fmt),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("a", ctypes.c_void_p), ("xv", ctypes.c_void_p),
+                ("y", ctypes.c_void_p), ("result", ctypes.c_void_p), ("alpha", ctypes.c_double),
+                ("beta", ctypes.c_double)]
+
+
+JOB_UNPACK, JOB_DOT, JOB_AXPY, JOB_GEMV_N, JOB_GEMV_T = 0, 1, 2, 3, 4
 
 
 def fmt(f) -> Fmt:
@@ -83,9 +96,17 @@ def lib() -> ctypes.CDLL:
                                               i64, i32, vp, sz, vp]
             L.flyte_refine_jacobi.argtypes = [i64, vp, i64, vp, Fmt, i64, vp, vp, dbl, i32, i32, vp, sz, vp,
                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+            L.flyte_batch_prepare.argtypes = [ctypes.POINTER(Job), i32, vp, sz, vp]
+            L.flyte_batch_workspace_bytes.argtypes = [ctypes.POINTER(Job), i32]
+            L.flyte_batch_workspace_bytes.restype = sz
+            L.flyte_batch_launch.argtypes = [vp, vp]
+            L.flyte_batch_autotune.argtypes = [vp, sz, vp]
+            L.flyte_batch_autotune_bytes.argtypes = []
+            L.flyte_batch_autotune_bytes.restype = sz
             for name in ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_scal",
                          "flyte_gemv", "flyte_gemv_packed_y", "flyte_gemv_static", "flyte_gemm",
-                         "flyte_gemm_packed_c", "flyte_refine_jacobi"):
+                         "flyte_gemm_packed_c", "flyte_refine_jacobi", "flyte_batch_prepare",
+                         "flyte_batch_launch", "flyte_batch_autotune"):
                 getattr(L, name).restype = i32
             L.flyte_workspace_bytes.argtypes = [ctypes.c_char_p, i64, i64, i64, Fmt]
             L.flyte_workspace_bytes.restype = sz
@@ -291,3 +312,34 @@ def refine_jacobi(A64: torch.Tensor, Ak: torch.Tensor, fa, b: torch.Tensor, x: t
                                      int(max_outer), int(inner), _ptr(ws), ws.numel(), _stream(stream),
                                      ctypes.byref(it), ctypes.byref(rr)))
     return it.value, rr.value
+
+
+def job(op: int, fx, n: int, a, y, *, fy=None, m: int = 0, xv=None, result=None, alpha: float = 0.0,
+        beta: float = 0.0, mode="rne") -> Job:
+    """A flyte_job from tensors or pointers."""
+    return Job(op, _mode(mode), fmt(fx), fmt(fy if fy is not None else fx), m, n, _ptr(a), _ptr(xv), _ptr(y),
+               _ptr(result), float(alpha), float(beta))
+
+
+def batch_prepare(jobs, ws: torch.Tensor | None = None, device=None, stream=None) -> torch.Tensor:
+    """Plan a batch and upload its tables; returns the workspace to pass to batch_launch."""
+    arr = (Job * len(jobs))(*jobs)
+    nbytes = lib().flyte_batch_workspace_bytes(arr, len(jobs))
+    if nbytes == ctypes.c_size_t(-1).value:
+        _check(lib().flyte_batch_prepare(arr, len(jobs), None, 0, _stream(stream)))
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device or "cuda")
+    _check(lib().flyte_batch_prepare(arr, len(jobs), _ptr(ws), ws.numel(), _stream(stream)))
+    return ws
+
+
+def batch_launch(ws: torch.Tensor, stream=None) -> None:
+    """Run a prepared batch (one persistent kernel; capturable in a CUDA graph)."""
+    _check(lib().flyte_batch_launch(_ptr(ws), _stream(stream)))
+
+
+def batch_autotune(device=None, stream=None) -> None:
+    """Measure the tile-size candidates of every (operation, k, base) and keep the fastest."""
+    nbytes = lib().flyte_batch_autotune_bytes()
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+    _check(lib().flyte_batch_autotune(_ptr(ws), nbytes, _stream(stream)))

@@ -183,3 +183,25 @@ def refine_system(n: int, seed_g: int = 8, seed_b: int = 9):
     A[np.arange(n), np.arange(n)] += n
     b = rng(seed_b).standard_normal(n)
     return A, b
+
+
+BATCH_FORMATS = [(k, 1) for k in range(2, 8)] + [(2, 0), (3, 0)]   # (k, base): double 2..7, float 2..3
+
+
+def batch_specs(njobs: int, seed: int = 5, len_range=(1e3, 1e6), side_range=(64, 4096)):
+    """Uneven jobs of the batched workload: op uniformly among unpack/dot/axpy/gemv N/gemv T, a
+    format from BATCH_FORMATS, vector lengths log-uniform in len_range and gemv sides log-uniform in
+    side_range.  Returns dicts {op, k, base, n, m} (op: 0 unpack, 1 dot, 2 axpy, 3 gemv N, 4 gemv T)."""
+    g = rng(seed)
+    out = []
+    for _ in range(njobs):
+        op = int(g.integers(0, 5))
+        k, base = BATCH_FORMATS[int(g.integers(0, len(BATCH_FORMATS)))]
+        if op <= 2:
+            n = int(np.exp(g.uniform(np.log(len_range[0]), np.log(len_range[1]))))
+            m = 0
+        else:
+            n = int(np.exp(g.uniform(np.log(side_range[0]), np.log(side_range[1]))))
+            m = int(np.exp(g.uniform(np.log(side_range[0]), np.log(side_range[1]))))
+        out.append({"op": op, "k": k, "base": base, "n": n, "m": m})
+    return out

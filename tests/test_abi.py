@@ -64,3 +64,15 @@ def test_zero_length_is_a_noop(lib):
     f = flyte.Fmt(3, 1)
     assert lib.flyte_pack(None, None, 0, f, 1, 1, 0, None) == 0
     assert lib.flyte_unpack(None, None, 0, f, 1, 1, None) == 0
+
+
+def test_batch_job_layout_and_host_validation(lib):
+    assert ctypes.sizeof(flyte.Job) == 88
+    bad = (flyte.Job * 1)(flyte.Job(9, 0, flyte.Fmt(3, 1), flyte.Fmt(3, 1), 0, 10, None, None, None, None, 0.0, 0.0))
+    assert lib.flyte_batch_workspace_bytes(bad, 1) == ctypes.c_size_t(-1).value
+    assert lib.flyte_batch_prepare(bad, 1, None, 0, None) == 1
+    assert b"job 0" in lib.flyte_last_error_string()
+    big = (flyte.Job * 1)(flyte.Job(3, 0, flyte.Fmt(3, 1), flyte.Fmt(3, 1), 4, 5000, 1, 1, 1, None, 1.0, 0.0))
+    assert lib.flyte_batch_prepare(big, 1, None, 0, None) == 2     # gemv side above the batch limit
+    ok = (flyte.Job * 1)(flyte.Job(0, 0, flyte.Fmt(3, 1), flyte.Fmt(3, 1), 0, 1000, 16, None, 16, None, 0.0, 0.0))
+    assert 0 < lib.flyte_batch_workspace_bytes(ok, 1) < 4096

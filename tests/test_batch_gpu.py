@@ -1,0 +1,157 @@
+"""GPU parity of the batched persistent launch (flyte_batch_prepare / flyte_batch_launch).
+
+Every job of a mixed batch is checked against the oracle with the bound of
+its single-job entry point: unpack and axpy bit-exact (NaN by class), dot
+within 4n 2^-53 sum|xy|, gemv within 4(len+2) 2^-53 (|alpha| sum|Ax| + |beta y|).
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1601_07789_gb300 import flyte, inputs
+from tests.gpu_util import sync
+
+pytestmark = pytest.mark.gpu
+EPS = 2.0 ** -53
+
+
+class Batch:
+    """Host data, device buffers and jobs for a list of specs (inputs.batch_specs)."""
+
+    def __init__(self, specs, seed=1, offset=0):
+        g = np.random.default_rng(seed)
+        self.specs = specs
+        self.host = []
+        self.dev = []
+        self.jobs = []
+        for s in specs:
+            op, k, base, n, m = s["op"], s["k"], s["base"], s["n"], s["m"]
+            dt = np.float32 if base == 0 else np.float64
+            fx = (k, base)
+            h = {}
+            d = {}
+            if op in (0, 1, 2):
+                h["x"] = oracle.pack(g.standard_normal(n).astype(dt), base, k)
+                d["x"] = self._dev(h["x"], offset)
+            if op == 0:
+                d["y"] = torch.zeros(n, dtype=torch.float32 if base == 0 else torch.float64, device="cuda")
+                job = flyte.job(flyte.JOB_UNPACK, fx, n, d["x"], d["y"])
+            elif op == 1:
+                h["y"] = oracle.pack(g.standard_normal(n).astype(dt), base, k)
+                d["y"] = self._dev(h["y"], offset)
+                d["r"] = torch.full((), np.nan, dtype=torch.float64, device="cuda")
+                job = flyte.job(flyte.JOB_DOT, fx, n, d["x"], d["y"], fy=fx, result=d["r"])
+            elif op == 2:
+                h["y"] = oracle.pack(g.standard_normal(n).astype(dt), base, k)
+                d["y"] = self._dev(h["y"], offset)
+                h["alpha"] = float(g.uniform(-2, 2))
+                job = flyte.job(flyte.JOB_AXPY, fx, n, d["x"], d["y"], fy=fx, alpha=h["alpha"], mode="rne")
+            else:
+                h["A"] = oracle.pack(g.standard_normal(m * n).astype(dt), base, k)
+                lx, ly = (n, m) if op == 3 else (m, n)
+                h["xv"] = g.standard_normal(lx)
+                h["y0"] = g.standard_normal(ly)
+                h["alpha"], h["beta"] = 1.5, -0.5
+                d["A"] = self._dev(h["A"], offset)
+                d["xv"] = torch.from_numpy(h["xv"]).cuda()
+                d["y"] = torch.from_numpy(h["y0"].copy()).cuda()
+                job = flyte.job(flyte.JOB_GEMV_N if op == 3 else flyte.JOB_GEMV_T, fx, n, d["A"], d["y"], m=m,
+                                xv=d["xv"], alpha=1.5, beta=-0.5)
+            self.host.append(h)
+            self.dev.append(d)
+            self.jobs.append(job)
+
+    @staticmethod
+    def _dev(a, offset):
+        buf = torch.zeros(a.size + offset + 16, dtype=torch.uint8, device="cuda")
+        buf[offset:offset + a.size] = torch.from_numpy(a).cuda()
+        return buf[offset:]
+
+    def check(self, skip_axpy=False):
+        for s, h, d in zip(self.specs, self.host, self.dev):
+            op, k, base, n, m = s["op"], s["k"], s["base"], s["n"], s["m"]
+            if op == 0:
+                got = d["y"].cpu().numpy()
+                want = oracle.unpack(h["x"], base, k).view(np.float32 if base == 0 else np.float64)
+                assert np.array_equal(got.view(want.dtype).view(np.uint8), want.view(np.uint8)), s
+            elif op == 1:
+                if n == 0:
+                    assert float(d["r"].item()) == 0.0
+                    continue
+                ref, _, absum = oracle.dot(n, h["x"], (base, k), 1, h["y"], (base, k), 1)
+                got = float(d["r"].item())
+                assert abs(got - ref) <= 4 * n * EPS * absum + 2 * EPS * abs(ref), s
+            elif op == 2 and not skip_axpy:
+                got = d["y"][: n * k].cpu().numpy()
+                want = oracle.axpy(n, h["alpha"], h["x"], (base, k), 1, h["y"], (base, k), 1, oracle.RNE)
+                assert np.array_equal(got, want), s
+            elif op >= 3:
+                trans = "N" if op == 3 else "T"
+                ref, absum = oracle.gemv(trans, m, n, 1.5, h["A"], (base, k), n, h["xv"], 1, -0.5, h["y0"], 1)
+                got = d["y"].cpu().numpy()
+                L = n if op == 3 else m
+                bound = 4 * (L + 2) * EPS * (1.5 * absum + 0.5 * np.abs(h["y0"])) + 2 * EPS * np.abs(ref)
+                assert np.all(np.abs(got - ref) <= bound), s
+
+
+SPECS = inputs.batch_specs(160, seed=5, len_range=(1, 2e5), side_range=(1, 700))
+
+
+def test_batch_mixed_jobs():
+    b = Batch(SPECS)
+    ws = flyte.batch_prepare(b.jobs)
+    flyte.batch_launch(ws)
+    sync()
+    b.check()
+
+
+def test_batch_replay_and_graph():
+    """Launching again (counters reset by the kernel) and replaying a captured CUDA graph give the same
+    results; axpy jobs are left out (they update in place)."""
+    specs = [s for s in SPECS if s["op"] != 2][:80]
+    b = Batch(specs, seed=2)
+    ws = flyte.batch_prepare(b.jobs)
+    flyte.batch_launch(ws)
+    sync()
+    b.check()
+    first = [d["y"].clone() if s["op"] != 1 else d["r"].clone() for s, d in zip(specs, b.dev)]
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        flyte.batch_launch(ws, stream=stream)
+    for _ in range(3):
+        for i, s in enumerate(specs):
+            if s["op"] >= 3:
+                b.dev[i]["y"].copy_(torch.from_numpy(b.host[i]["y0"]))
+        graph.replay()
+        sync()
+        again = [d["y"] if s["op"] != 1 else d["r"] for s, d in zip(specs, b.dev)]
+        for a, c in zip(first, again):
+            assert torch.equal(a, c)
+
+
+def test_batch_misaligned_and_edges():
+    specs = [{"op": op, "k": k, "base": base, "n": n, "m": m}
+             for (op, k, base, n, m) in [(0, 3, 1, 1001, 0), (1, 5, 1, 999, 0), (2, 7, 1, 1003, 0), (3, 3, 1, 77, 65),
+                                         (4, 6, 1, 63, 130), (1, 2, 0, 4097, 0), (0, 3, 0, 7, 0), (1, 4, 1, 0, 0),
+                                         (3, 2, 1, 5, 0), (4, 5, 1, 3, 1)]]
+    b = Batch(specs, seed=3, offset=1)
+    ws = flyte.batch_prepare(b.jobs)
+    flyte.batch_launch(ws)
+    sync()
+    b.check()
+    with pytest.raises(flyte.FlyteError):
+        flyte.batch_prepare([flyte.job(flyte.JOB_GEMV_N, (4, 1), 5000, b.dev[0]["x"], b.dev[0]["x"], m=4,
+                                       xv=b.dev[0]["x"])])   # gemv side above the batch limit
+
+
+def test_batch_autotune_then_run():
+    flyte.batch_autotune()
+    b = Batch(SPECS[:60], seed=4)
+    ws = flyte.batch_prepare(b.jobs)
+    flyte.batch_launch(ws)
+    sync()
+    b.check()
