@@ -44,10 +44,12 @@ struct JobDev {
   int64_t tiles, part_base;
   int32_t fast;                               // dot/gemv: double-word path proven; unpack/axpy: group path
   int32_t fold_rows;                          // gemv 'T'
+  int32_t row_chunks;                         // gemv 'T': row chunks per column block
+  int32_t done_base;                          // first completion counter of the job
 };
 
 struct Header {
-  int32_t njobs, nitems;
+  int32_t njobs, nitems, ndone, pad;
   int64_t off_jobs, off_items, off_parts, off_done;
   int32_t counter;   // next tile to take
   int32_t exited;    // blocks that have finished
@@ -57,7 +59,8 @@ int64_t up256(int64_t b) { return (b + 255) & ~int64_t(255); }
 
 // ---- tile table ----------------------------------------------------------------------------
 
-// tile size per (op, base, k): elements (UNPACK, DOT, AXPY), rows (GEMV_N); 'T' tiles are 1024 columns
+// tile size per (op, base, k): elements (UNPACK, DOT, AXPY), rows (GEMV_N, and the row chunk of the
+// 1024-column 'T' tiles)
 std::mutex g_tune_mu;
 int64_t g_tile[kNOps][2][9];
 bool g_tile_init = false;
@@ -68,7 +71,7 @@ int64_t default_tile(int op) {
     case FLYTE_JOB_DOT: return 65536;
     case FLYTE_JOB_AXPY: return 65536;
     case FLYTE_JOB_GEMV_N: return 16;
-    default: return 1024;
+    default: return 256;
   }
 }
 
@@ -325,8 +328,14 @@ __device__ void gemv_n_tile(const JobDev& jd, int64_t r0, int64_t r1, float* x1,
       }
       for (int64_t c = n / 4 * 4 + lane; c < n; c += 32)
         fold_elem<BASE, K>(widen<BASE, K>(load_code_bytes<K>(Ar + c * K)), x1[c], x2[c], acc[0], ok);
-      const DW s = dw_warp_sum(dw_sum4(acc[0], acc[1], acc[2], acc[3]));
-      t = __shfl_sync(0xFFFFFFFFu, dw_value(s), 0);
+      if (jd.fast == 1) {
+        // long rows: double-word tree, one conversion
+        const DW s = dw_warp_sum(dw_sum4(acc[0], acc[1], acc[2], acc[3]));
+        t = __shfl_sync(0xFFFFFFFFu, dw_value(s), 0);
+      } else {
+        // short rows: the four slots and the warp reduced in binary64 (a tighter bound)
+        t = warp_sum(dw_value(acc[0]) + dw_value(acc[1]) + dw_value(acc[2]) + dw_value(acc[3]));
+      }
       good = __all_sync(0xFFFFFFFFu, ok) && isfinite(t);
     }
     if (!good) {
@@ -338,32 +347,37 @@ __device__ void gemv_n_tile(const JobDev& jd, int64_t r0, int64_t r1, float* x1,
   }
 }
 
-// Columns [c0, c1) of y <- alpha A^T x + beta y: thread t owns columns c0 + 4t .. + 3 over all rows.
+// Tile (column block cb, row chunk rc) of y <- alpha A^T x + beta y: thread t owns columns
+// 1024 cb + 4t .. + 3 over rows [r0, r1) and writes their partial sums; the block that completes the
+// column block's last row chunk adds the chunks in order and applies the epilogue.
 template <int BASE, int K>
-__device__ void gemv_t_tile(const JobDev& jd, int64_t c0, int64_t c1, float* x1, float* x2) {
-  const int64_t m = jd.j.m, n = jd.j.n;
+__device__ void gemv_t_tile(const JobDev& jd, int tile, int64_t r0, int64_t r1, float* x1, float* x2,
+                            double* parts, int* done, int* s_last) {
+  const int64_t n = jd.j.n;
   const uint8_t* A = static_cast<const uint8_t*>(jd.j.a);
   const double* x = jd.j.xv;
   double* y = static_cast<double*>(jd.j.y);
+  const int nrc = jd.row_chunks;
+  const int cb = tile / nrc, rc = tile % nrc;
+  const int64_t c0 = int64_t(cb) * (4 * kBThreads);
   if (jd.fast) {
-    split_x(x, m, x1, x2);
+    split_x(x + r0, r1 - r0, x1, x2);
     __syncthreads();
   }
   const int64_t c = c0 + 4 * threadIdx.x;
-  if (c >= c1) return;
-  const int nc = int(min(int64_t(4), c1 - c));
+  const int nc = int(max(int64_t(0), min(int64_t(4), n - c)));
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  bool ok = jd.fast && nc == 4 && ((n * K) % group_bytes(K)) == 0;
+  bool ok = jd.fast && nc == 4;
   if (ok) {
     DW acc[2][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) dw_zero(acc[0][q]), dw_zero(acc[1][q]);
     const uint8_t* colp = A + c * K;
     int since = 0;
-    for (int64_t i = 0; i < m; ++i) {
+    for (int64_t i = r0; i < r1; ++i) {
       uint32_t w[K];
       load_group<K>(colp + i * n * K, w);
-      const float a1 = x1[i], a2 = x2[i];
+      const float a1 = x1[i - r0], a2 = x2[i - r0];
 #pragma unroll
       for (int q = 0; q < 4; ++q) fold_elem<BASE, K>(extract_widened<BASE, K>(w, q), a1, a2, acc[i & 1][q], ok);
       if (++since == jd.fold_rows) {
@@ -385,18 +399,33 @@ __device__ void gemv_t_tile(const JobDev& jd, int64_t c0, int64_t c1, float* x1,
   if (!ok) {
     for (int q = 0; q < nc; ++q) {
       double s2 = 0.0;
-      for (int64_t i = 0; i < m; ++i) s2 = fma(code_to_double<BASE, K>(load_code_bytes<K>(A + (i * n + c + q) * K)), x[i], s2);
+      for (int64_t i = r0; i < r1; ++i)
+        s2 = fma(code_to_double<BASE, K>(load_code_bytes<K>(A + (i * n + c + q) * K)), x[i], s2);
       v[q] = s2;
     }
   }
-  for (int q = 0; q < nc; ++q) y[c + q] = gemv_epilogue(v[q], jd.j.alpha, jd.j.beta, y + c + q);
+  double* mine = parts + jd.part_base + (int64_t(cb) * nrc + rc) * (4 * kBThreads) + 4 * threadIdx.x;
+  for (int q = 0; q < nc; ++q) mine[q] = v[q];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_last = atomicAdd(&done[jd.done_base + cb], 1) == nrc - 1;
+  __syncthreads();
+  if (*s_last) {
+    __threadfence();
+    const double* col = parts + jd.part_base + int64_t(cb) * nrc * (4 * kBThreads) + 4 * threadIdx.x;
+    for (int q = 0; q < nc; ++q) {
+      double t = 0.0;
+      for (int r = 0; r < nrc; ++r) t += __ldcg(col + int64_t(r) * (4 * kBThreads) + q);
+      y[c + q] = gemv_epilogue(t, jd.j.alpha, jd.j.beta, y + c + q);
+    }
+  }
 }
 
 // ---- the persistent kernel ----------------------------------------------------------------
 
 __global__ void __launch_bounds__(kBThreads) batch_kernel(uint8_t* __restrict__ ws) {
   extern __shared__ __align__(16) float xs[];   // x1, x2 of the current gemv tile
-  __shared__ int s_item;
+  __shared__ int s_item, s_last;
   __shared__ double s_red[kBWarps];
   Header* h = reinterpret_cast<Header*>(ws);
   const JobDev* jobs = reinterpret_cast<const JobDev*>(ws + h->off_jobs);
@@ -433,7 +462,7 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(uint8_t* __restrict__ 
       if (threadIdx.x == 0) {
         parts[jd.part_base + item.tile] = v;
         __threadfence();
-        if (atomicAdd(&done[item.job], 1) == int(jd.tiles) - 1) {
+        if (atomicAdd(&done[jd.done_base], 1) == int(jd.tiles) - 1) {
           __threadfence();
           double s = 0.0;
           for (int64_t t = 0; t < jd.tiles; ++t) s += __ldcg(&parts[jd.part_base + t]);
@@ -443,7 +472,9 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(uint8_t* __restrict__ 
     } else if (op == FLYTE_JOB_GEMV_N) {
       with_fmt(jd.j.fx, [&]<int B, int K>() { gemv_n_tile<B, K>(jd, item.begin, item.end, xs, xs + kMaxSide); });
     } else {
-      with_fmt(jd.j.fx, [&]<int B, int K>() { gemv_t_tile<B, K>(jd, item.begin, item.end, xs, xs + kMaxSide); });
+      with_fmt(jd.j.fx, [&]<int B, int K>() {
+        gemv_t_tile<B, K>(jd, item.tile, item.begin, item.end, xs, xs + kMaxSide, parts, done, &s_last);
+      });
     }
     __syncthreads();   // shared x and s_red are reused by the next tile
   }
@@ -452,7 +483,7 @@ __global__ void __launch_bounds__(kBThreads) batch_kernel(uint8_t* __restrict__ 
   if (threadIdx.x == 0) {
     __threadfence();
     if (atomicAdd(&h->exited, 1) == int(gridDim.x) - 1) {
-      for (int i = 0; i < h->njobs; ++i) done[i] = 0;
+      for (int i = 0; i < h->ndone; ++i) done[i] = 0;
       h->counter = 0;
       __threadfence();
       h->exited = 0;
@@ -470,6 +501,7 @@ struct Plan {
   std::vector<JobDev> jobs;
   std::vector<Item> items;
   int64_t nparts = 0;
+  int32_t ndone = 0;
   int64_t bytes = 0;
   Header hdr{};
 };
@@ -531,22 +563,36 @@ flyte_status make_plan(const flyte_job* jobs, int njobs, Plan& p) {
       const int K = j.fx.k;
       const bool al = aligned_to(j.a, group_bytes(K)) && (j.n * K) % group_bytes(K) == 0;
       if (op == FLYTE_JOB_GEMV_N) {
-        // chains of n/128 + 1 terms per slot, double-word tree 2 + 5, one binary64 step
+        // chains of n/128 + 1 terms per slot; then a double-word tree (2 + 5 levels, one binary64
+        // step) or, for rows too short for its bound, binary64 (3 + 5 levels)
         const int64_t L = j.n / 128 + 2;
-        d.fast = al && dw_bound_ok(j.n, L, 1, 14, 7) ? 1 : 0;
+        d.fast = !al ? 0 : (dw_bound_ok(j.n, L, 1, 14, 7) ? 1 : (dw_bound_ok(j.n, L, 9, 14) ? 2 : 0));
         add_items(j.m, tile);
       } else {
-        // parity chains of fold/2 + 1 terms folded into binary64 every fold rows
+        // tiles: 1024-column blocks x chunks of `tile` rows; parity chains of fold/2 + 1 terms folded
+        // into binary64 every fold rows; binary64 levels: the folds of a chunk, then the chunks in order
+        const int64_t rows = std::max<int64_t>(4, tile);
+        const int64_t nrc = (j.m + rows - 1) / rows;
+        const int64_t ncb = (j.n + 4 * kBThreads - 1) / (4 * kBThreads);
         d.fast = 0;
         d.fold_rows = 64;
         for (int64_t f = 64; f >= 2 && al; f /= 2) {
-          if (dw_bound_ok(j.m, f / 2 + 1, 2 * (j.m / f) + 4, 14)) {
+          if (dw_bound_ok(j.m, f / 2 + 1, 2 * (rows / f) + 4 + nrc, 14)) {
             d.fast = 1;
             d.fold_rows = int32_t(f);
             break;
           }
         }
-        add_items(j.n, 4 * kBThreads);
+        d.row_chunks = int32_t(nrc);
+        int32_t t = 0;
+        for (int64_t cb = 0; cb < ncb; ++cb)
+          for (int64_t rc = 0; rc < nrc; ++rc, ++t)
+            p.items.push_back(Item{i, t, rc * rows, std::min(j.m, (rc + 1) * rows)});
+        d.tiles = t;
+        d.part_base = p.nparts;
+        p.nparts += ncb * nrc * 4 * kBThreads;
+        d.done_base = p.ndone;
+        p.ndone += int32_t(ncb);
       }
     } else {
       if (j.n == 0) continue;
@@ -566,16 +612,19 @@ flyte_status make_plan(const flyte_job* jobs, int njobs, Plan& p) {
       if (op == FLYTE_JOB_DOT) {
         d.part_base = p.nparts;
         p.nparts += d.tiles;
+        d.done_base = p.ndone;
+        p.ndone += 1;
       }
     }
   }
   p.hdr.njobs = njobs;
   p.hdr.nitems = int32_t(p.items.size());
+  p.hdr.ndone = p.ndone;
   p.hdr.off_jobs = 256;
   p.hdr.off_items = p.hdr.off_jobs + up256(int64_t(sizeof(JobDev)) * njobs);
   p.hdr.off_parts = p.hdr.off_items + up256(int64_t(sizeof(Item)) * int64_t(p.items.size()));
   p.hdr.off_done = p.hdr.off_parts + up256(8 * p.nparts);
-  p.bytes = p.hdr.off_done + up256(4 * int64_t(njobs));
+  p.bytes = p.hdr.off_done + up256(4 * int64_t(p.ndone));
   return FLYTE_OK;
 }
 
@@ -664,7 +713,7 @@ constexpr int64_t kTuneJobs = 16;
 constexpr int64_t kTuneLen = int64_t(1) << 18;   // elements per streaming job
 constexpr int64_t kTuneSide = 1024;               // gemv jobs: 1024 x 1024
 constexpr int64_t kTuneData = 2 * kTuneJobs * kTuneLen * 8 + kTuneJobs * kTuneLen * 8;   // x, y streams, outputs
-constexpr int64_t kTuneWs = int64_t(1) << 20;
+constexpr int64_t kTuneWs = int64_t(8) << 20;
 
 }  // namespace
 
@@ -686,9 +735,9 @@ flyte_status batch_autotune(void* ws, size_t ws_bytes, cudaStream_t s) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return cuda_status(cudaGetLastError(), "batch autotune");
   flyte_status result = FLYTE_OK;
-  for (int op : {FLYTE_JOB_UNPACK, FLYTE_JOB_DOT, FLYTE_JOB_AXPY, FLYTE_JOB_GEMV_N}) {
+  for (int op : {FLYTE_JOB_UNPACK, FLYTE_JOB_DOT, FLYTE_JOB_AXPY, FLYTE_JOB_GEMV_N, FLYTE_JOB_GEMV_T}) {
     for (const flyte_fmt& f : fmts) {
-      const bool gemv = op == FLYTE_JOB_GEMV_N;
+      const bool gemv = op == FLYTE_JOB_GEMV_N || op == FLYTE_JOB_GEMV_T;
       const int64_t len = gemv ? kTuneSide * kTuneSide : kTuneLen;
       const int64_t njob = gemv ? (kTuneJobs * kTuneLen * 8) / (len * f.k) : kTuneJobs;
       fill_codes<<<grid_for(njob * len, 256), 256, 0, s>>>(xs, njob * len, f.k, f.base, 11u);
@@ -719,7 +768,8 @@ flyte_status batch_autotune(void* ws, size_t ws_bytes, cudaStream_t s) {
       }
       const int64_t cands_stream[3] = {16384, 65536, 262144};
       const int64_t cands_rows[3] = {8, 16, 32};
-      const int64_t* cands = gemv ? cands_rows : cands_stream;
+      const int64_t cands_chunks[3] = {128, 256, 512};
+      const int64_t* cands = op == FLYTE_JOB_GEMV_T ? cands_chunks : (gemv ? cands_rows : cands_stream);
       int64_t best = cands[1];
       float best_ms = 1e30f;
       for (int c = 0; c < 3 && result == FLYTE_OK; ++c) {

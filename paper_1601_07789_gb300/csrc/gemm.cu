@@ -178,14 +178,28 @@ __device__ __forceinline__ void store_c(double* C, const COut& co, int64_t idx, 
   store_code_bytes_rt(p, narrow_rt<FLYTE_F64>(uint64_t(__double_as_longlong(r)), co.kc, co.mode), co.kc);
 }
 
-// Warps [0, E): epilogue (fold each K chunk's accumulator into fp32 registers,
-// then write C); warp E: TMA producer; warp E + 1: MMA issuer and TMEM owner.
-// The tensor core accumulates a chunk of k-blocks into one of two TMEM
-// buffers while the epilogue warps drain the other.  Its binary32
-// accumulation is biased (measured: errors grow with the number of MMA steps
-// into one accumulator, about one ulp of the partial sum per step), so a
-// chunk holds at most 16 (one product) or 16-24 (split formats) MMA steps and
-// the chunks are added with round-to-nearest in registers.
+// Persistent: one CTA per SM walks the output tiles tau = blockIdx.x,
+// blockIdx.x + gridDim.x, ... in groups of kGroupRows tile rows (column by
+// column inside a group, so that concurrently running CTAs share A and B
+// tiles in L2).  Warps [0, E): epilogue (fold each K chunk's accumulator into
+// fp32 registers, then write C); warp E: TMA producer; warp E + 1: MMA issuer
+// and TMEM owner.  The stage ring and the two TMEM chunk buffers run on
+// across tiles, so the next tile's loads and MMAs overlap this tile's C
+// store.  The tensor core's binary32 accumulation is biased (measured: errors
+// grow with the number of MMA steps into one accumulator, about one ulp of
+// the partial sum per step), so a chunk holds at most 16 (one product) or
+// 16-24 (split formats) MMA steps and the chunks are added with
+// round-to-nearest in registers.
+constexpr int kGroupRows = 16;
+
+__device__ __forceinline__ void tile_of(int64_t tau, int64_t mt, int64_t nt, int64_t& tm, int64_t& tn) {
+  const int64_t per_group = int64_t(kGroupRows) * nt;
+  const int64_t g = tau / per_group, r = tau % per_group;
+  const int64_t rows = min(int64_t(kGroupRows), mt - g * kGroupRows);
+  tm = g * kGroupRows + r % rows;
+  tn = r / rows;
+}
+
 template <int K>
 __global__ void __launch_bounds__(GemmCfg<K>::kThreads) gemm_tc_kernel(const __grid_constant__ PartMaps maps,
                                                                        int64_t m, int64_t n, int64_t kdim,
@@ -202,11 +216,13 @@ __global__ void __launch_bounds__(GemmCfg<K>::kThreads) gemm_tc_kernel(const __g
   uint64_t* accempty = accfull + 2;     // 2: chunk accumulator drained
   uint64_t* mdone = accempty + 2;       // every MMA has completed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mdone + 1);
+  uint32_t* issued = tslot + 1;         // k-blocks the producer issued (for the drain after a failure)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = int64_t(blockIdx.y) * kBM, n0 = int64_t(blockIdx.x) * BN;
   const int KB = int((kdim + kBK - 1) / kBK);
   constexpr int kChunkBlocks = Cfg::kChunkBlocks;
   const int NC = (KB + kChunkBlocks - 1) / kChunkBlocks;
+  const int64_t mt = (m + kBM - 1) / kBM, nt = (n + BN - 1) / BN;
+  const int64_t ntiles = mt * nt;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -218,6 +234,7 @@ __global__ void __launch_bounds__(GemmCfg<K>::kThreads) gemm_tc_kernel(const __g
       mbar_init(&accempty[b], E);
     }
     mbar_init(mdone, 1);
+    *issued = 0;
     mbar_init_fence();
   }
   __syncwarp();
@@ -232,76 +249,109 @@ __global__ void __launch_bounds__(GemmCfg<K>::kThreads) gemm_tc_kernel(const __g
 
   if (warp == E) {
     if (lane == 0) {
-      for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb % S;
-        if (kb >= S && !mbar_wait(&empty[s], uint32_t(((kb / S) - 1) & 1), status)) break;
-        mbar_arrive_expect_tx(&full[s], Cfg::kStage);
+      uint32_t it = 0;
+      bool ok = true;
+      for (int64_t tau = blockIdx.x; tau < ntiles && ok; tau += gridDim.x) {
+        int64_t tm, tn;
+        tile_of(tau, mt, nt, tm, tn);
+        for (int kb = 0; kb < KB; ++kb, ++it) {
+          const int s = int(it % S);
+          if (it >= S && !mbar_wait(&empty[s], ((it / S) - 1) & 1, status)) { ok = false; break; }
+          mbar_arrive_expect_tx(&full[s], Cfg::kStage);
 #pragma unroll
-        for (int p = 0; p < NP; ++p) tma_load_2d(a_tile(s, p), &maps.a[p], kb * kBK, int(m0), &full[s]);
+          for (int p = 0; p < NP; ++p) tma_load_2d(a_tile(s, p), &maps.a[p], kb * kBK, int(tm * kBM), &full[s]);
 #pragma unroll
-        for (int p = 0; p < NP; ++p) tma_load_2d(b_tile(s, p), &maps.b[p], kb * kBK, int(n0), &full[s]);
+          for (int p = 0; p < NP; ++p) tma_load_2d(b_tile(s, p), &maps.b[p], kb * kBK, int(tn * BN), &full[s]);
+        }
       }
+      *issued = it;
     }
   } else if (warp == E + 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = umma_idesc_bf16(kBM, BN);
       bool ok = true;
-      for (int c = 0; c < NC && ok; ++c) {
-        const int b = c & 1;
-        if (c >= 2 && !mbar_wait(&accempty[b], uint32_t(((c >> 1) - 1) & 1), status)) break;
-        tc_fence_after();
-        const uint32_t acc = tmem + uint32_t(b * BN);
-        const int kb_end = min(KB, (c + 1) * kChunkBlocks);
-        for (int kb = c * kChunkBlocks; kb < kb_end; ++kb) {
-          const int s = kb % S;
-          if (!mbar_wait(&full[s], uint32_t((kb / S) & 1), status)) { ok = false; break; }
+      uint32_t it = 0, g = 0;   // k-blocks and chunks so far
+      for (int64_t tau = blockIdx.x; tau < ntiles && ok; tau += gridDim.x) {
+        for (int c = 0; c < NC && ok; ++c, ++g) {
+          const int b = int(g & 1);
+          if (g >= 2 && !mbar_wait(&accempty[b], ((g >> 1) - 1) & 1, status)) { ok = false; break; }
           tc_fence_after();
+          const uint32_t acc = tmem + uint32_t(b * BN);
+          const int kb_end = min(KB, (c + 1) * kChunkBlocks);
+          for (int kb = c * kChunkBlocks; kb < kb_end; ++kb, ++it) {
+            const int s = int(it % S);
+            if (!mbar_wait(&full[s], (it / S) & 1, status)) { ok = false; break; }
+            tc_fence_after();
 #pragma unroll
-          for (int q = 0; q < Cfg::kNProd; ++q) {
-            const int pa = NP == 1 ? 0 : (NP == 2 ? kProdA2[q] : kProdA[q]);
-            const int pb = NP == 1 ? 0 : (NP == 2 ? kProdB2[q] : kProdB[q]);
-            const uint64_t ad = umma_desc_kmajor_sw128(smem_addr(a_tile(s, pa)));
-            const uint64_t bd = umma_desc_kmajor_sw128(smem_addr(b_tile(s, pb)));
+            for (int q = 0; q < Cfg::kNProd; ++q) {
+              const int pa = NP == 1 ? 0 : (NP == 2 ? kProdA2[q] : kProdA[q]);
+              const int pb = NP == 1 ? 0 : (NP == 2 ? kProdB2[q] : kProdB[q]);
+              const uint64_t ad = umma_desc_kmajor_sw128(smem_addr(a_tile(s, pa)));
+              const uint64_t bd = umma_desc_kmajor_sw128(smem_addr(b_tile(s, pb)));
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk)
-              umma_bf16(acc, ad + 2 * kk, bd + 2 * kk, idesc,
-                        (kb > c * kChunkBlocks || q > 0 || kk > 0) ? 1u : 0u);
+              for (int kk = 0; kk < kBK / 16; ++kk)
+                umma_bf16(acc, ad + 2 * kk, bd + 2 * kk, idesc,
+                          (kb > c * kChunkBlocks || q > 0 || kk > 0) ? 1u : 0u);
+            }
+            umma_commit(&empty[s]);
           }
-          umma_commit(&empty[s]);
+          if (ok) umma_commit(&accfull[b]);
         }
-        if (ok) umma_commit(&accfull[b]);
       }
       umma_commit(mdone);    // fires once every MMA issued above has completed
     }
   } else {
     // epilogue warp: TMEM lanes 32 * (warp % 4) .. + 31, columns 64 * (warp / 4) .. + 63
     const int quarter = warp & 3, cblk = warp >> 2;
-    float total[64];
-#pragma unroll
-    for (int i = 0; i < 64; ++i) total[i] = 0.f;
     bool ok = true;
-    for (int c = 0; c < NC; ++c) {
-      const int b = c & 1;
-      ok = mbar_wait(&accfull[b], uint32_t((c >> 1) & 1), status);
-      if (!__all_sync(0xFFFFFFFFu, ok)) { ok = false; break; }
-      tc_fence_after();
+    uint32_t g = 0;
+    for (int64_t tau = blockIdx.x; tau < ntiles && ok; tau += gridDim.x) {
+      int64_t tm, tn;
+      tile_of(tau, mt, nt, tm, tn);
+      float total[64];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        uint32_t r[16];
-        tmem_ld16(tmem + (uint32_t(32 * quarter) << 16) + uint32_t(b * BN + 64 * cblk + 16 * j), r);
+      for (int i = 0; i < 64; ++i) total[i] = 0.f;
+      for (int c = 0; c < NC; ++c, ++g) {
+        const int b = int(g & 1);
+        ok = mbar_wait(&accfull[b], (g >> 1) & 1, status);
+        if (!__all_sync(0xFFFFFFFFu, ok)) { ok = false; break; }
+        tc_fence_after();
 #pragma unroll
-        for (int i = 0; i < 16; ++i) total[16 * j + i] = __fadd_rn(total[16 * j + i], __uint_as_float(r[i]));
+        for (int j = 0; j < 8; ++j) {
+          uint32_t r[8];
+          tmem_ld8(tmem + (uint32_t(32 * quarter) << 16) + uint32_t(b * BN + 64 * cblk + 8 * j), r);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) total[8 * j + i] = __fadd_rn(total[8 * j + i], __uint_as_float(r[i]));
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&accempty[b]);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&accempty[b]);
-    }
-    const int64_t row = m0 + 32 * quarter + lane;
-    if (ok && row < m) {
-      const int64_t base = row * ldc + n0 + 64 * cblk;
+      if (!ok) break;
+      const int64_t row = tm * kBM + 32 * quarter + lane;
+      const int64_t col0 = tn * BN + 64 * cblk;
+      if (row < m && col0 < n) {
+        const int64_t base = row * ldc + col0;
+        if (co.q == nullptr && col0 + 64 <= n && (reinterpret_cast<uintptr_t>(C + base) & 15) == 0) {
+          float4* out = reinterpret_cast<float4*>(C + base);
 #pragma unroll
-      for (int i = 0; i < 64; ++i) {
-        if (n0 + 64 * cblk + i < n) store_c(C, co, base + i, total[i], alpha, beta);
+          for (int i = 0; i < 16; ++i) {
+            float4 v = make_float4(alpha * total[4 * i], alpha * total[4 * i + 1], alpha * total[4 * i + 2],
+                                   alpha * total[4 * i + 3]);
+            if (beta != 0.f) {
+              const float4 o = out[i];
+              v = make_float4(__fmaf_rn(alpha, total[4 * i], beta * o.x), __fmaf_rn(alpha, total[4 * i + 1], beta * o.y),
+                              __fmaf_rn(alpha, total[4 * i + 2], beta * o.z),
+                              __fmaf_rn(alpha, total[4 * i + 3], beta * o.w));
+            }
+            out[i] = v;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 64; ++i) {
+            if (col0 + i < n) store_c(C, co, base + i, total[i], alpha, beta);
+          }
+        }
       }
     }
   }
@@ -311,7 +361,9 @@ __global__ void __launch_bounds__(GemmCfg<K>::kThreads) gemm_tc_kernel(const __g
     if (lane == 0) {
       mbar_wait(mdone, 0, nullptr);
       if (*reinterpret_cast<volatile int*>(status) != 0) {
-        for (int kb = (KB > S ? KB - S : 0); kb < KB; ++kb) mbar_wait(&full[kb % S], uint32_t((kb / S) & 1), nullptr);
+        const uint32_t n_is = *issued;
+        for (uint32_t j = n_is > uint32_t(S) ? n_is - S : 0; j < n_is; ++j)
+          mbar_wait(&full[j % S], (j / S) & 1, nullptr);
       }
     }
     __syncwarp();
@@ -508,7 +560,8 @@ flyte_status launch_tc(int64_t m, int64_t n, int64_t kdim, double alpha, const u
   if (cudaFuncSetAttribute(gemm_tc_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem) !=
       cudaSuccess)
     return cuda_status(cudaGetLastError(), "gemm");
-  dim3 grid(unsigned((n + Cfg::BN - 1) / Cfg::BN), unsigned((m + kBM - 1) / kBM));
+  const int64_t tiles = ((m + kBM - 1) / kBM) * ((n + Cfg::BN - 1) / Cfg::BN);
+  const unsigned grid = unsigned(min(tiles, int64_t(sm_count())));   // persistent: one CTA per SM
   gemm_tc_kernel<K><<<grid, Cfg::kThreads, Cfg::kSmem, s>>>(maps, m, n, kdim, float(alpha), float(beta), C, ldc,
                                                             co, status);
   FLYTE_TRY_LAUNCH("gemm");
