@@ -28,6 +28,10 @@
 namespace flyte {
 namespace {
 
+#ifndef FLYTE_GEMM_CHUNK1
+#define FLYTE_GEMM_CHUNK1 4            // k-blocks per TMEM chunk for one-part formats
+#endif
+
 constexpr int kBM = 128;
 constexpr int kBK = 64;                // bf16 elements per row of a stage tile (128 bytes)
 constexpr int kSmemBudget = 200 * 1024;
@@ -127,7 +131,7 @@ struct GemmCfg {
   static constexpr int kEpiWarps = 4 * (BN / 64);            // each owns 32 rows x 64 columns
   static constexpr int kThreads = 32 * (kEpiWarps + 2);      // + producer warp + MMA warp
   // k-blocks accumulated in TMEM before folding: at most 16-24 MMA steps per chunk
-  static constexpr int kChunkBlocks = NP == 1 ? 4 : 1;
+  static constexpr int kChunkBlocks = NP == 1 ? FLYTE_GEMM_CHUNK1 : 1;
 };
 
 // Part products in issue order: smallest first and the large (0,0) product
