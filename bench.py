@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--no-rows", action="store_true", help="skip the per-row measurements")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=6144, help="rows of the CPU-baseline sample")
-    ap.add_argument("--case", choices=["gemv", "convert", "blas1", "gemm"],
+    ap.add_argument("--case", choices=["gemv", "convert", "blas1", "gemm", "batch"],
                     help="run one small invocation of these kernels (for profilers) and exit; no JSON line")
     ap.add_argument("--k", type=int, default=6, help="byte width for --case")
     ap.add_argument("--size", type=int, default=8192, help="matrix side (gemv, gemm) for --case")
@@ -95,6 +95,36 @@ def run_case(args):
         for _ in range(2):
             flyte.dot(xs, (k, 1), ys, (k, 1))
             flyte.axpy(1e-9, xs, (k, 1), ys, (k, 1))
+    elif args.case == "batch":
+        from paper_1601_07789_gb300 import inputs
+        specs = inputs.batch_specs(512, seed=5)
+        pools = {f: flyte.pack(torch.randn(1 << 24, dtype=torch.float32 if f[1] == 0 else torch.float64, device=dev,
+                                           generator=gen), f[0]) for f in inputs.BATCH_FORMATS}
+        xv = torch.randn(4096, dtype=torch.float64, device=dev, generator=gen)
+        jobs, keep = [], []
+        for sp in specs:
+            f = (sp["k"], sp["base"])
+            n_, m_ = sp["n"], sp["m"]
+            if sp["op"] == 0:
+                out = torch.empty(n_, dtype=torch.float32 if f[1] == 0 else torch.float64, device=dev)
+                keep.append(out)
+                jobs.append(flyte.job(flyte.JOB_UNPACK, f, n_, pools[f], out))
+            elif sp["op"] == 1:
+                r = torch.empty((), dtype=torch.float64, device=dev)
+                keep.append(r)
+                jobs.append(flyte.job(flyte.JOB_DOT, f, n_, pools[f], pools[f], fy=f, result=r))
+            elif sp["op"] == 2:
+                yy = pools[f][: n_ * f[0]].clone()
+                keep.append(yy)
+                jobs.append(flyte.job(flyte.JOB_AXPY, f, n_, pools[f], yy, fy=f, alpha=1e-9))
+            else:
+                yy = torch.zeros(max(m_, n_), dtype=torch.float64, device=dev)
+                keep.append(yy)
+                jobs.append(flyte.job(flyte.JOB_GEMV_N if sp["op"] == 3 else flyte.JOB_GEMV_T, f, n_, pools[f], yy,
+                                      m=m_, xv=xv, alpha=1.0, beta=0.0))
+        ws = flyte.batch_prepare(jobs, device=dev)
+        for _ in range(2):
+            flyte.batch_launch(ws)
     elif args.case == "gemm":
         base = 0 if k <= 4 else 1
         dt = torch.float32 if base == 0 else torch.float64
@@ -457,17 +487,28 @@ def run_e2e(args, codes, x, y, ws, dev, dist, world):
     dy = torch.empty_like(y)
     steps = max(1, min(args.steps, 20))
     stream = torch.cuda.current_stream()
+    copy_stream = torch.cuda.Stream(device=dev)
+    landed = {k: torch.cuda.Event() for k in KS}
+    done = torch.cuda.Event()
 
     def step():
+        # the copies run on their own stream and each width's gemvs start as soon as its matrix
+        # has landed, so copies of the next widths overlap the compute of the current one
+        copy_stream.wait_event(done)
+        with torch.cuda.stream(copy_stream):
+            dx.copy_(hx, non_blocking=True)
+            dy.copy_(hy, non_blocking=True)
+            for k in KS:
+                dA[k].copy_(host[k], non_blocking=True)
+                landed[k].record(copy_stream)
         for k in KS:
-            dA[k].copy_(host[k], non_blocking=True)
-        dx.copy_(hx, non_blocking=True)
-        dy.copy_(hy, non_blocking=True)
-        for k in KS:
+            stream.wait_event(landed[k])
             for t in "NT":
                 flyte.gemv(t, M, N, ALPHA, dA[k], (k, 1), N, dx, BETA, dy, ws=ws[t])
         out_y.copy_(dy, non_blocking=True)
+        done.record(stream)
 
+    done.record(stream)
     for _ in range(2):
         step()
     torch.cuda.synchronize()
@@ -532,7 +573,8 @@ def run_rows(dev, hbm_peak):
     wsd = torch.empty(flyte.workspace_bytes("dot", 0, n, 0, (4, 1)), dtype=torch.uint8, device=dev)
     rows["dot_f64_k4"] = entry(2 * 4 * n, timeit(lambda: flyte.dot(xs, (4, 1), ys, (4, 1), n=n, out=res, ws=wsd)),
                                2 * n)
-    rows["axpy_f64_k4"] = entry(3 * 4 * n, timeit(lambda: flyte.axpy(1e-9, xs, (4, 1), ys, (4, 1), n=n)), 2 * n)
+    rows["axpy_f64_k4"] = entry(3 * 4 * n, timeit(lambda: flyte.axpy(1.5, xs, (4, 1), ys, (4, 1), n=n)), 2 * n)
+    rows["axpy_f64_k4_alpha_not_binary32"] = entry(3 * 4 * n, timeit(lambda: flyte.axpy(1e-9 + 1e-25, xs, (4, 1), ys, (4, 1), n=n)), 2 * n)
     rows["n"] = n
     del v, out, xs, ys
     rows.update(run_gemm_rows(dev))

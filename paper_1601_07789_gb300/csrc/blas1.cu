@@ -17,6 +17,8 @@
 //
 // scal: x <- pack(alpha * x) in place (the paper's in-place "scale"
 // benchmark, Sec. 6), with the product rounded once in the native type.
+#include <cmath>
+
 #include "dwacc.cuh"
 
 namespace flyte {
@@ -163,6 +165,111 @@ __global__ void __launch_bounds__(kThreads) axpy_groups(const uint8_t* __restric
   }
 }
 
+// ---- axpy without binary64 arithmetic -------------------------------------------------
+//
+// binary64 FMAs run at a small fraction of the binary32 rate on this GPU and
+// bound the kernel above (its fp64 pipe is ~82 % busy at a third of the HBM
+// rate).  When alpha is a binary32 number (1.5, -2, 0.75, ...) and the
+// format is double-based with k <= 4 (x, y then have <= 21 significant bits
+// and are exact binary32 numbers inside the window), s = alpha x + y is
+// obtained EXACTLY as h + L + Le with error-free transformations on the
+// binary32 pipe, and the code of pack(RN64(s)) is decided from it:
+//   p + e = alpha x (TwoProd), s1 + t1 = p + y, s2 + t2 = t1 + e,
+//   h + l = s1 + s2, L + Le = l + t2               (TwoSum each; all exact)
+// The k-byte result keeps the top m = 8k - 12 mantissa bits of h (magnitude
+// code Q) and depends only on the sign of f - B, where f u_h = (dropped bits
+// of h) u_h + L + Le is the exact remainder above Q's value and B is 0
+// (toward zero, round to odd) or half a code ulp (nearest even, half-up).
+// That sign is read exactly from w = RN((D - B) u_h + L) and Le.  RN64(s)
+// can differ from s only by 2^-27 u_h, so it cannot move s across a boundary
+// unless s lies within that distance of it; such elements (|w| <= 2^-20 u_h,
+// not exactly on the boundary), exact zeros and anything outside the window
+// send their group to the binary64 FMA instead.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+template <int K>
+__device__ __forceinline__ bool axpy_exact_f32(uint64_t ux, uint64_t uy, float af, int mode, uint64_t& code) {
+  constexpr int m = 8 * K - 12;          // mantissa bits of the code
+  constexpr int d = 23 - m;              // bits of h below the code's last bit
+  float xf, yf, unused;
+  bool ok = dbl_to_pair<K>(uint32_t(ux >> 32), 0u, xf, unused);
+  ok &= dbl_to_pair<K>(uint32_t(uy >> 32), 0u, yf, unused);
+  if (!ok) return false;
+  const float p = __fmul_rn(af, xf);
+  const float e = __fmaf_rn(af, xf, -p);
+  float s1, t1, s2, t2, h, l, L, Le;
+  two_sum(p, yf, s1, t1);
+  two_sum(t1, e, s2, t2);
+  two_sum(s1, s2, h, l);
+  two_sum(l, t2, L, Le);
+  const uint32_t hb = __float_as_uint(h);
+  const uint32_t E = (hb >> 23) & 0xFFu;
+  if (E < 24u) return false;             // zero or too small for the exact code path
+  const uint32_t M = hb & 0x7FFFFFu;
+  const uint32_t D = M & ((1u << d) - 1u);
+  const uint64_t Q = (uint64_t(E + 896u) << m) | (M >> d);
+  const float uh = __uint_as_float((E - 23u) << 23);
+  const bool neg = hb >> 31;
+  const float Lm = neg ? -L : L, Lem = neg ? -Le : Le;
+  const bool nearest = mode == FLYTE_RNE || mode == FLYTE_HALF_UP;
+  const float B = nearest ? float(1u << (d - 1)) : 0.f;
+  const float Df = __fsub_rn(__uint_as_float(0x4B000000u | D), 8388608.0f);   // D exactly
+  const float z = __fmul_rn(__fsub_rn(Df, B), uh);                             // (D - B) u_h exactly
+  const float w = __fadd_rn(z, Lm);
+  int sg;                                                                      // sign of f - B
+  if (w != 0.f) {
+    if (fabsf(w) <= __fmul_rn(uh, 0x1p-20f)) return false;
+    sg = w > 0.f ? 1 : -1;
+  } else {
+    if (Lem != 0.f) return false;
+    sg = 0;
+  }
+  uint64_t q;
+  switch (mode) {
+    case FLYTE_RNE: q = sg < 0 ? Q : (sg > 0 ? Q + 1 : Q + (Q & 1)); break;
+    case FLYTE_RTZ: q = sg < 0 ? Q - 1 : Q; break;
+    case FLYTE_HALF_UP: q = sg < 0 ? Q : Q + 1; break;
+    default: q = sg == 0 ? Q : ((sg < 0 ? Q - 1 : Q) | 1u); break;     // round to odd
+  }
+  code = (uint64_t(neg) << (8 * K - 1)) | q;
+  return true;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads) axpy_groups_f32exact(const uint8_t* __restrict__ X,
+                                                                 uint8_t* __restrict__ Y, int64_t ngrp,
+                                                                 double alpha, int mode) {
+  const float af = float(alpha);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngrp; g += stride) {
+    uint32_t wx[K], wy[K], wo[K];
+    load_group<K>(X + g * (4 * K), wx);
+    load_group_rw<K>(Y + g * (4 * K), wy);
+#pragma unroll
+    for (int j = 0; j < K; ++j) wo[j] = 0;
+    uint64_t c[4];
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      ok &= axpy_exact_f32<K>(extract_widened<FLYTE_F64, K>(wx, q), extract_widened<FLYTE_F64, K>(wy, q), af, mode,
+                              c[q]);
+    if (!ok) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        c[q] = axpy_one<FLYTE_F64, K>(extract_widened<FLYTE_F64, K>(wx, q), extract_widened<FLYTE_F64, K>(wy, q),
+                                      alpha, af, mode);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) deposit_code<K>(wo, q, c[q]);
+    store_group<K>(Y + g * (4 * K), wo);
+  }
+}
+
 // Any widths of one base, strides and alignments: one element per thread.
 template <int BASE, int KY>
 __global__ void __launch_bounds__(kThreads) axpy_generic(const uint8_t* __restrict__ X, int kx, int64_t incx,
@@ -282,7 +389,16 @@ flyte_status launch_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, i
     const int S = group_bytes(KY);
     if (fx.k == KY && incx == 1 && incy == 1 && aligned(x, S) && aligned(y, S) && n >= 4) {
       const int64_t ngrp = n / 4;
-      axpy_groups<BASE, KY><<<grid_for(ngrp, kThreads), kThreads, 0, s>>>(X, Y, ngrp, alpha, mode);
+      bool done = false;
+      if constexpr (BASE == FLYTE_F64 && KY >= 2 && KY <= 4) {
+        // alpha a binary32 number inside the window: the exact binary32 path
+        const float af = float(alpha);
+        if (double(af) == alpha && std::fabs(alpha) >= 0x1p-40 && std::fabs(alpha) < 0x1p40) {
+          axpy_groups_f32exact<KY><<<grid_for(ngrp, kThreads), kThreads, 0, s>>>(X, Y, ngrp, alpha, mode);
+          done = true;
+        }
+      }
+      if (!done) axpy_groups<BASE, KY><<<grid_for(ngrp, kThreads), kThreads, 0, s>>>(X, Y, ngrp, alpha, mode);
       FLYTE_TRY_LAUNCH("axpy");
       first = ngrp * 4;
     }

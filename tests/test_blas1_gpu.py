@@ -246,3 +246,30 @@ def test_scal_config_mixture_and_paths():
         check_scal(got, m, 2.75, xs, f, inc, "rne")
     with pytest.raises(flyte.FlyteError):
         flyte.scal(1.0, torch.zeros(16, dtype=torch.uint8, device="cuda"), (9, 1), n=2)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("mode", MODES)
+def test_axpy_binary32_alpha_exact_path(k, mode):
+    """alpha exactly representable in binary32 takes the binary32 error-free path for double-based
+    k <= 4: bit-exact against the oracle on data that make exact results, ties, cancellations and
+    out-of-window values (which fall back to binary64) frequent."""
+    f = (k, 1)
+    g = np.random.default_rng(40 + k)
+    n = 1 << 16
+    xv = g.standard_normal(n)
+    yv = g.standard_normal(n)
+    yv[::7] = -1.5 * xv[::7]                                   # cancellation (exact zero for alpha = 1.5)
+    yv[1::11] = 0.0
+    xv[2::13] *= 2.0 ** g.integers(-60, 60, xv[2::13].size)   # outside the window for some
+    xs = _stream(xv, f)
+    ys = _stream(yv, f)
+    for alpha in (1.5, -2.0, 0.75, 3.0, -0.3125, 1.0, 2.0 ** -30):
+        got = run_axpy(n, alpha, xs, f, 1, ys, f, 1, mode)
+        check_axpy(got, n, alpha, xs, f, 1, ys, f, 1, mode)
+    # small integers: many exactly representable sums and exact midpoints
+    xi = _stream(g.integers(-64, 64, n).astype(np.float64), f)
+    yi = _stream(g.integers(-4096, 4096, n).astype(np.float64) * 0.5, f)
+    for alpha in (1.5, 0.5, 3.0):
+        got = run_axpy(n, alpha, xi, f, 1, yi, f, 1, mode)
+        check_axpy(got, n, alpha, xi, f, 1, yi, f, 1, mode)
