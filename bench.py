@@ -260,13 +260,19 @@ def init_dist(world, local):
     return None
 
 
-def max_over_ranks(dist, v: float) -> float:
+def max_over_ranks(dist, v: float, device: str = "cuda") -> float:
+    """The largest value over the ranks (every rank gets it); v itself without a process group."""
     if dist is None:
         return v
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(world: int, steps: int, bytes_per_step: int, elapsed_ms: float) -> float:
+    """Whole-job GB/s of `world` replicas that each ran `steps` steps, over the slowest rank's time."""
+    return world * steps * bytes_per_step / (elapsed_ms * 1e-3) / 1e9
 
 
 # ---- CPU oracle sample ------------------------------------------------------------------
@@ -392,7 +398,7 @@ def run_flyte(args):
     clocks = sampler.summary()
 
     per_call_ms = {c: statistics.mean(a.elapsed_time(b) for a, b in ev[c]) for c in calls}
-    value = world * args.steps * step_bytes() / (elapsed_ms * 1e-3) / 1e9
+    value = replica_value(world, args.steps, step_bytes(), elapsed_ms)
 
     # native binary64 gemv on the same GPU (cuBLAS through torch) and our own k = 8
     Am = A64.view(M, N)
@@ -457,8 +463,8 @@ def run_flyte(args):
 
     if not args.no_e2e:
         out["e2e"] = run_e2e(args, codes, x, y, ws, dev, dist, world)
-    if not args.no_rows:
-        out["rows"] = run_rows(dev, hbm_peak)
+    if not args.no_rows and rank == 0:
+        out["rows"] = run_rows(dev, hbm_peak)   # per-row figures: rank 0 only
     del A64, codes
     if rank == 0 and world == 1:
         gbs, dt, desc = oracle_sample(args.cpu_rows)
@@ -523,7 +529,7 @@ def run_e2e(args, codes, x, y, ws, dev, dist, world):
     torch.cuda.synchronize()
     ms = max_over_ranks(dist, e0.elapsed_time(e1))
     h2d = sum(host[k].numel() for k in KS) + hx.numel() * 8 + hy.numel() * 8
-    return {"value": round(world * steps * step_bytes() / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+    return {"value": round(replica_value(world, steps, step_bytes(), ms), 1), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": out_y.numel() * 8, "steps": steps,
             "ms_per_step": round(ms / steps, 3)}
 
