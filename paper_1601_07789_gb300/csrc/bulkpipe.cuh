@@ -1,11 +1,14 @@
-// bulkpipe.cuh -- warp-private multi-stage pipelines of bulk copies into shared memory.
+// bulkpipe.cuh -- mbarrier and bulk-copy primitives of the shared-memory rings.
 //
-// A warp owns S stages of shared memory, each with one mbarrier.  For each
-// stage one lane arms the barrier with the number of bytes expected, a few
-// lanes issue cp.async.bulk copies (global -> shared, completion counted on
-// the barrier), and later all lanes wait on the barrier's phase before
-// reading the stage.  Keeping S - 1 stages in flight per warp makes the bytes
-// in flight per SM independent of register pressure and occupancy.
+// A ring has S stages of shared memory, each with a "full" mbarrier (and,
+// when producer and consumers are different warps, an "empty" one).  For
+// each stage a producer lane arms the full barrier with the number of bytes
+// expected, producer lanes issue cp.async.bulk copies (global -> shared,
+// completion counted on the barrier), and the consumers wait on the
+// barrier's phase before reading the stage, then arrive on the empty
+// barrier.  Keeping S - 1 stages in flight makes the bytes in flight per SM
+// independent of register pressure and occupancy (gemv 'N'; the gemm uses
+// the same barriers with TMA tensor copies).
 //
 // Every wait is bounded: after 200 ms (or kWaitLimit polls, or as soon as
 // another warp has already recorded a failure) the waiting lane records an
