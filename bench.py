@@ -94,7 +94,8 @@ def run_case(args):
         ys = flyte.pack(torch.randn(n, dtype=torch.float64, device=dev, generator=gen), k)
         for _ in range(2):
             flyte.dot(xs, (k, 1), ys, (k, 1))
-            flyte.axpy(1e-9, xs, (k, 1), ys, (k, 1))
+            flyte.axpy(1.5, xs, (k, 1), ys, (k, 1))      # binary32 alpha: the exact binary32 path
+            flyte.axpy(1e-9, xs, (k, 1), ys, (k, 1))     # any other alpha: binary64 fma
     elif args.case == "batch":
         from paper_1601_07789_gb300 import inputs
         specs = inputs.batch_specs(512, seed=5)

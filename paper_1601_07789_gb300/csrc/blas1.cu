@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(kThreads) axpy_groups(const uint8_t* __restric
 // obtained EXACTLY as h + L + Le with error-free transformations on the
 // binary32 pipe, and the code of pack(RN64(s)) is decided from it:
 //   p + e = alpha x (TwoProd), s1 + t1 = p + y, s2 + t2 = t1 + e,
-//   h + l = s1 + s2, L + Le = l + t2               (TwoSum each; all exact)
+//   h + l = s1 + s2, L + Le = l + t2               (TwoSum each; all exact;
+//   Le is formed only when needed, see below)
 // The k-byte result keeps the top m = 8k - 12 mantissa bits of h (magnitude
 // code Q) and depends only on the sign of f - B, where f u_h = (dropped bits
 // of h) u_h + L + Le is the exact remainder above Q's value and B is 0
@@ -192,58 +193,63 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
-template <int K>
-__device__ __forceinline__ bool axpy_exact_f32(uint64_t ux, uint64_t uy, float af, int mode, uint64_t& code) {
+template <int K, int MODE>
+__device__ __forceinline__ bool axpy_exact_f32(uint64_t ux, uint64_t uy, float af, uint64_t& code) {
   constexpr int m = 8 * K - 12;          // mantissa bits of the code
   constexpr int d = 23 - m;              // bits of h below the code's last bit
+  constexpr bool kNearest = MODE == FLYTE_RNE || MODE == FLYTE_HALF_UP;
+  constexpr float kB = kNearest ? float(1u << (d - 1)) : 0.f;   // boundary, in ulps of h
   float xf, yf, unused;
   bool ok = dbl_to_pair<K>(uint32_t(ux >> 32), 0u, xf, unused);
   ok &= dbl_to_pair<K>(uint32_t(uy >> 32), 0u, yf, unused);
-  if (!ok) return false;
   const float p = __fmul_rn(af, xf);
   const float e = __fmaf_rn(af, xf, -p);
-  float s1, t1, s2, t2, h, l, L, Le;
+  float s1, t1, s2, t2, h, l;
   two_sum(p, yf, s1, t1);
   two_sum(t1, e, s2, t2);
   two_sum(s1, s2, h, l);
-  two_sum(l, t2, L, Le);
+  // s = h + l + t2 exactly.  t2 != 0 needs p + y inexact, hence no cancellation in it, so
+  // |t2| <= 2^-24 ulp(s1) and |l + t2| <= ulp(h) / 2 + tiny: L = RN(l + t2) errs by at most
+  // 2^-24 ulp(h), far inside the 2^-20 ulp(h) guard below; the exact error is formed only when a
+  // decision falls on a boundary.
+  const float L = __fadd_rn(l, t2);
   const uint32_t hb = __float_as_uint(h);
   const uint32_t E = (hb >> 23) & 0xFFu;
-  if (E < 24u) return false;             // zero or too small for the exact code path
+  ok &= E >= 24u;                        // zero or too small for the exact code path: binary64
   const uint32_t M = hb & 0x7FFFFFu;
   const uint32_t D = M & ((1u << d) - 1u);
   const uint64_t Q = (uint64_t(E + 896u) << m) | (M >> d);
-  const float uh = __uint_as_float((E - 23u) << 23);
+  const float uh = __uint_as_float(max(E, 24u) - 23u << 23);
   const bool neg = hb >> 31;
-  const float Lm = neg ? -L : L, Lem = neg ? -Le : Le;
-  const bool nearest = mode == FLYTE_RNE || mode == FLYTE_HALF_UP;
-  const float B = nearest ? float(1u << (d - 1)) : 0.f;
   const float Df = __fsub_rn(__uint_as_float(0x4B000000u | D), 8388608.0f);   // D exactly
-  const float z = __fmul_rn(__fsub_rn(Df, B), uh);                             // (D - B) u_h exactly
-  const float w = __fadd_rn(z, Lm);
-  int sg;                                                                      // sign of f - B
-  if (w != 0.f) {
-    if (fabsf(w) <= __fmul_rn(uh, 0x1p-20f)) return false;
-    sg = w > 0.f ? 1 : -1;
-  } else {
-    if (Lem != 0.f) return false;
+  const float z = __fmul_rn(__fsub_rn(Df, kB), uh);                            // (D - B) u_h exactly
+  const float w = __fadd_rn(z, neg ? -L : L);
+  int sg = (w > 0.f) - (w < 0.f);                                              // sign of f - B
+  if (!(fabsf(w) > __fmul_rn(uh, 0x1p-20f))) {
+    // within the guard: decided only if exactly on the boundary
+    float L2, Le;
+    two_sum(l, t2, L2, Le);
+    ok &= w == 0.f && Le == 0.f;
     sg = 0;
   }
   uint64_t q;
-  switch (mode) {
-    case FLYTE_RNE: q = sg < 0 ? Q : (sg > 0 ? Q + 1 : Q + (Q & 1)); break;
-    case FLYTE_RTZ: q = sg < 0 ? Q - 1 : Q; break;
-    case FLYTE_HALF_UP: q = sg < 0 ? Q : Q + 1; break;
-    default: q = sg == 0 ? Q : ((sg < 0 ? Q - 1 : Q) | 1u); break;     // round to odd
+  if constexpr (MODE == FLYTE_RNE) {
+    q = sg < 0 ? Q : (sg > 0 ? Q + 1 : Q + (Q & 1));
+  } else if constexpr (MODE == FLYTE_RTZ) {
+    q = sg < 0 ? Q - 1 : Q;
+  } else if constexpr (MODE == FLYTE_HALF_UP) {
+    q = sg < 0 ? Q : Q + 1;
+  } else {
+    q = sg == 0 ? Q : ((sg < 0 ? Q - 1 : Q) | 1u);                            // round to odd
   }
   code = (uint64_t(neg) << (8 * K - 1)) | q;
-  return true;
+  return ok;
 }
 
-template <int K>
+template <int K, int MODE>
 __global__ void __launch_bounds__(kThreads) axpy_groups_f32exact(const uint8_t* __restrict__ X,
                                                                  uint8_t* __restrict__ Y, int64_t ngrp,
-                                                                 double alpha, int mode) {
+                                                                 double alpha) {
   const float af = float(alpha);
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngrp; g += stride) {
@@ -256,17 +262,28 @@ __global__ void __launch_bounds__(kThreads) axpy_groups_f32exact(const uint8_t* 
     bool ok = true;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-      ok &= axpy_exact_f32<K>(extract_widened<FLYTE_F64, K>(wx, q), extract_widened<FLYTE_F64, K>(wy, q), af, mode,
-                              c[q]);
+      ok &= axpy_exact_f32<K, MODE>(extract_widened<FLYTE_F64, K>(wx, q), extract_widened<FLYTE_F64, K>(wy, q), af,
+                                    c[q]);
     if (!ok) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         c[q] = axpy_one<FLYTE_F64, K>(extract_widened<FLYTE_F64, K>(wx, q), extract_widened<FLYTE_F64, K>(wy, q),
-                                      alpha, af, mode);
+                                      alpha, af, MODE);
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) deposit_code<K>(wo, q, c[q]);
     store_group<K>(Y + g * (4 * K), wo);
+  }
+}
+
+template <int K>
+void launch_axpy_f32exact(const uint8_t* X, uint8_t* Y, int64_t ngrp, double alpha, int mode, cudaStream_t s) {
+  const unsigned grid = grid_for(ngrp, kThreads);
+  switch (mode) {
+    case FLYTE_RNE: axpy_groups_f32exact<K, FLYTE_RNE><<<grid, kThreads, 0, s>>>(X, Y, ngrp, alpha); break;
+    case FLYTE_RTZ: axpy_groups_f32exact<K, FLYTE_RTZ><<<grid, kThreads, 0, s>>>(X, Y, ngrp, alpha); break;
+    case FLYTE_HALF_UP: axpy_groups_f32exact<K, FLYTE_HALF_UP><<<grid, kThreads, 0, s>>>(X, Y, ngrp, alpha); break;
+    default: axpy_groups_f32exact<K, FLYTE_RTO><<<grid, kThreads, 0, s>>>(X, Y, ngrp, alpha); break;
   }
 }
 
@@ -394,7 +411,7 @@ flyte_status launch_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, i
         // alpha a binary32 number inside the window: the exact binary32 path
         const float af = float(alpha);
         if (double(af) == alpha && std::fabs(alpha) >= 0x1p-40 && std::fabs(alpha) < 0x1p40) {
-          axpy_groups_f32exact<KY><<<grid_for(ngrp, kThreads), kThreads, 0, s>>>(X, Y, ngrp, alpha, mode);
+          launch_axpy_f32exact<KY>(X, Y, ngrp, alpha, mode, s);
           done = true;
         }
       }
