@@ -93,8 +93,10 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 // 16384 x 16384, double-based k = 3..6:
 //  - 'N' runs the persistent producer/consumer ring below for every k when A
 //    is 16-byte aligned (k = 4: 0.298 -> 0.233 ms, k = 5: 0.377 -> 0.338 ms),
-//    8 consumer warps of 2 rows, 512 columns per stage, tiles of up to 4096
-//    columns (8 warps of 4 rows or 16 warps of 2 rows were slower); the
+//    8 consumer warps of 2 rows, 512 columns per stage and two blocks per SM
+//    for k <= 4, 1024 columns per stage and one block per SM for k > 4
+//    (k = 5: 0.338 -> 0.332 ms), tiles of up to 4096 columns (8 warps of 4
+//    rows, 16 warps of 2 rows, 256-column stages were slower); the
 //    direct kernel (2 or 4 groups per lane and step) serves the rest;
 //  - 'T' loads 4 rows per step and prefetches the next step while folding
 //    the current one.  A producer/consumer ring for 'T' (8 rows per stage)
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 #define FLYTE_PC_COLS_SMALL_K 512      // columns per ring stage, k <= 4
 #endif
 #ifndef FLYTE_PC_COLS_LARGE_K
-#define FLYTE_PC_COLS_LARGE_K 512      // columns per ring stage, k > 4
+#define FLYTE_PC_COLS_LARGE_K 1024     // columns per ring stage, k = 5, 6
 #endif
 #ifndef FLYTE_PC_CHUNK
 #define FLYTE_PC_CHUNK 4096            // columns per 'N' tile (at most)
@@ -475,7 +477,10 @@ __global__ void __launch_bounds__(256) gemv_t_finish_packed(const double* __rest
 #define FLYTE_PC_ROWS 2                // rows per consumer warp
 #endif
 #ifndef FLYTE_PC_SMEM
-#define FLYTE_PC_SMEM 115456           // ring budget per block: two blocks per SM
+#define FLYTE_PC_SMEM 115456           // ring budget per block, k <= 4: two blocks per SM
+#endif
+#ifndef FLYTE_PC_SMEM_LARGE_K
+#define FLYTE_PC_SMEM_LARGE_K 200000   // ring budget per block, k > 4: one block per SM
 #endif
 
 constexpr int kPcWarps = FLYTE_PC_WARPS;
@@ -485,12 +490,15 @@ constexpr int kPcThreads = (kPcWarps + 1) * 32;
 static_assert(kPcRowsBlock + 2 <= 64, "the producer warp issues at most two copies per lane and stage");
 
 template <int K>
-__host__ __device__ constexpr int pc_cols() { return K <= 4 ? FLYTE_PC_COLS_SMALL_K : FLYTE_PC_COLS_LARGE_K; }
+__host__ __device__ constexpr int pc_cols() {
+  // k = 7, 8 keep 512 columns: two stages of 1024 would not fit in shared memory
+  return K <= 4 ? FLYTE_PC_COLS_SMALL_K : (K <= 6 ? FLYTE_PC_COLS_LARGE_K : 512);
+}
 template <int K>
 __host__ __device__ constexpr int pc_stage_bytes() { return 8 * pc_cols<K>() + kPcRowsBlock * pc_cols<K>() * K; }
 template <int K>
 __host__ __device__ constexpr int pc_stages() {
-  constexpr int s = FLYTE_PC_SMEM / pc_stage_bytes<K>();
+  constexpr int s = (K <= 4 ? FLYTE_PC_SMEM : FLYTE_PC_SMEM_LARGE_K) / pc_stage_bytes<K>();
   return s < 2 ? 2 : (s > 8 ? 8 : s);
 }
 template <int K>
