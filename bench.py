@@ -117,7 +117,7 @@ def run_case(args):
             elif sp["op"] == 2:
                 yy = pools[f][: n_ * f[0]].clone()
                 keep.append(yy)
-                jobs.append(flyte.job(flyte.JOB_AXPY, f, n_, pools[f], yy, fy=f, alpha=1e-9))
+                jobs.append(flyte.job(flyte.JOB_AXPY, f, n_, pools[f], yy, fy=f, alpha=1.5))
             else:
                 yy = torch.zeros(max(m_, n_), dtype=torch.float64, device=dev)
                 keep.append(yy)
@@ -724,8 +724,8 @@ def run_batch_rows(dev):
         elif op == 2:
             y = pool[: n * k].clone()
             keep.append(y)
-            jobs.append(flyte.job(flyte.JOB_AXPY, f, n, pool, y, fy=f, alpha=1e-9))
-            calls.append(lambda n=n, f=f, y=y, pool=pool: flyte.axpy(1e-9, pool, f, y, f, n=n))
+            jobs.append(flyte.job(flyte.JOB_AXPY, f, n, pool, y, fy=f, alpha=1.5))
+            calls.append(lambda n=n, f=f, y=y, pool=pool: flyte.axpy(1.5, pool, f, y, f, n=n))
             total_bytes += 3 * n * k
         else:
             trans = "N" if op == 3 else "T"

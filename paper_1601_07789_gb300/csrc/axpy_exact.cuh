@@ -1,0 +1,89 @@
+// axpy_exact.cuh -- the binary64-free exact axpy element (used by blas1.cu and batch.cu).
+//
+// binary64 FMAs run at a small fraction of the binary32 rate on this GPU and
+// bound the kernel above (its fp64 pipe is ~82 % busy at a third of the HBM
+// rate).  When alpha is a binary32 number (1.5, -2, 0.75, ...) and the
+// format is double-based with k <= 4 (x, y then have <= 21 significant bits
+// and are exact binary32 numbers inside the window), s = alpha x + y is
+// obtained EXACTLY as h + L + Le with error-free transformations on the
+// binary32 pipe, and the code of pack(RN64(s)) is decided from it:
+//   p + e = alpha x (TwoProd), s1 + t1 = p + y, s2 + t2 = t1 + e,
+//   h + l = s1 + s2, L + Le = l + t2               (TwoSum each; all exact;
+//   Le is formed only when needed, see below)
+// The k-byte result keeps the top m = 8k - 12 mantissa bits of h (magnitude
+// code Q) and depends only on the sign of f - B, where f u_h = (dropped bits
+// of h) u_h + L + Le is the exact remainder above Q's value and B is 0
+// (toward zero, round to odd) or half a code ulp (nearest even, half-up).
+// That sign is read exactly from w = RN((D - B) u_h + L) and Le.  RN64(s)
+// can differ from s only by 2^-27 u_h, so it cannot move s across a boundary
+// unless s lies within that distance of it; such elements (|w| <= 2^-20 u_h,
+// not exactly on the boundary), exact zeros and anything outside the window
+// send their group to the binary64 FMA instead.
+#pragma once
+
+#include "dwacc.cuh"
+
+namespace flyte {
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+template <int K, int MODE>
+__device__ __forceinline__ bool axpy_exact_f32(uint64_t ux, uint64_t uy, float af, uint64_t& code) {
+  constexpr int m = 8 * K - 12;          // mantissa bits of the code
+  constexpr int d = 23 - m;              // bits of h below the code's last bit
+  constexpr bool kNearest = MODE == FLYTE_RNE || MODE == FLYTE_HALF_UP;
+  constexpr float kB = kNearest ? float(1u << (d - 1)) : 0.f;   // boundary, in ulps of h
+  float xf, yf, unused;
+  bool ok = dbl_to_pair<K>(uint32_t(ux >> 32), 0u, xf, unused);
+  ok &= dbl_to_pair<K>(uint32_t(uy >> 32), 0u, yf, unused);
+  const float p = __fmul_rn(af, xf);
+  const float e = __fmaf_rn(af, xf, -p);
+  float s1, t1, s2, t2, h, l;
+  two_sum(p, yf, s1, t1);
+  two_sum(t1, e, s2, t2);
+  two_sum(s1, s2, h, l);
+  // s = h + l + t2 exactly.  t2 != 0 needs p + y inexact, hence no cancellation in it, so
+  // |t2| <= 2^-24 ulp(s1) and |l + t2| <= ulp(h) / 2 + tiny: L = RN(l + t2) errs by at most
+  // 2^-24 ulp(h), far inside the 2^-20 ulp(h) guard below; the exact error is formed only when a
+  // decision falls on a boundary.
+  const float L = __fadd_rn(l, t2);
+  const uint32_t hb = __float_as_uint(h);
+  const uint32_t E = (hb >> 23) & 0xFFu;
+  ok &= E >= 24u;                        // zero or too small for the exact code path: binary64
+  const uint32_t M = hb & 0x7FFFFFu;
+  const uint32_t D = M & ((1u << d) - 1u);
+  const uint64_t Q = (uint64_t(E + 896u) << m) | (M >> d);
+  const float uh = __uint_as_float(max(E, 24u) - 23u << 23);
+  const bool neg = hb >> 31;
+  const float Df = __fsub_rn(__uint_as_float(0x4B000000u | D), 8388608.0f);   // D exactly
+  const float z = __fmul_rn(__fsub_rn(Df, kB), uh);                            // (D - B) u_h exactly
+  const float w = __fadd_rn(z, neg ? -L : L);
+  int sg = (w > 0.f) - (w < 0.f);                                              // sign of f - B
+  if (!(fabsf(w) > __fmul_rn(uh, 0x1p-20f))) {
+    // within the guard: decided only if exactly on the boundary
+    float L2, Le;
+    two_sum(l, t2, L2, Le);
+    ok &= w == 0.f && Le == 0.f;
+    sg = 0;
+  }
+  uint64_t q;
+  if constexpr (MODE == FLYTE_RNE) {
+    q = sg < 0 ? Q : (sg > 0 ? Q + 1 : Q + (Q & 1));
+  } else if constexpr (MODE == FLYTE_RTZ) {
+    q = sg < 0 ? Q - 1 : Q;
+  } else if constexpr (MODE == FLYTE_HALF_UP) {
+    q = sg < 0 ? Q : Q + 1;
+  } else {
+    q = sg == 0 ? Q : ((sg < 0 ? Q - 1 : Q) | 1u);                            // round to odd
+  }
+  code = (uint64_t(neg) << (8 * K - 1)) | q;
+  return ok;
+}
+
+
+}  // namespace flyte

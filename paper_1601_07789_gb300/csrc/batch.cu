@@ -20,10 +20,12 @@
 //
 // Tile sizes come from a per-(operation, base, k) table: built-in defaults,
 // replaced by the fastest candidates that flyte_batch_autotune measures.
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
 
+#include "axpy_exact.cuh"
 #include "dwacc.cuh"
 
 namespace flyte {
@@ -174,6 +176,37 @@ __device__ __forceinline__ uint64_t axpy_elem(typename Native<BASE>::bits ux, ty
   }
 }
 
+// Groups [b/4, e/4) with the exact binary32 element of axpy_exact.cuh (alpha a binary32 number,
+// double-based k <= 4; the host sets fast = 2), binary64 for a group that needs it.
+template <int K, int MODE>
+__device__ void axpy_groups_exact(const JobDev& jd, int64_t b, int64_t e) {
+  const uint8_t* X = static_cast<const uint8_t*>(jd.j.a);
+  uint8_t* Y = static_cast<uint8_t*>(jd.j.y);
+  const float af = __double2float_rn(jd.j.alpha);
+  for (int64_t g = b / 4 + threadIdx.x; g < e / 4; g += kBThreads) {
+    uint32_t wx[K], wy[K], wo[K];
+    load_group<K>(X + g * (4 * K), wx);
+    load_group_rw<K>(Y + g * (4 * K), wy);
+#pragma unroll
+    for (int j = 0; j < K; ++j) wo[j] = 0;
+    uint64_t c[4];
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      ok &= axpy_exact_f32<K, MODE>(extract_widened<FLYTE_F64, K>(wx, q), extract_widened<FLYTE_F64, K>(wy, q), af,
+                                    c[q]);
+    if (!ok) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        c[q] = axpy_elem<FLYTE_F64, K>(extract_widened<FLYTE_F64, K>(wx, q), extract_widened<FLYTE_F64, K>(wy, q),
+                                       jd.j.alpha, MODE);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) deposit_code<K>(wo, q, c[q]);
+    store_group<K>(Y + g * (4 * K), wo);
+  }
+}
+
 // y has format (BASE, K); x has the same base and width kx (any)
 template <int BASE, int K>
 __device__ void axpy_tile(const JobDev& jd, int64_t b, int64_t e) {
@@ -183,7 +216,18 @@ __device__ void axpy_tile(const JobDev& jd, int64_t b, int64_t e) {
   uint8_t* Y = static_cast<uint8_t*>(jd.j.y);
   const int kx = jd.j.fx.k;
   int64_t i0 = b;
-  if (jd.fast) {
+  if constexpr (BASE == FLYTE_F64 && K >= 2 && K <= 4) {
+    if (jd.fast == 2) {
+      switch (jd.j.mode) {
+        case FLYTE_RNE: axpy_groups_exact<K, FLYTE_RNE>(jd, b, e); break;
+        case FLYTE_RTZ: axpy_groups_exact<K, FLYTE_RTZ>(jd, b, e); break;
+        case FLYTE_HALF_UP: axpy_groups_exact<K, FLYTE_HALF_UP>(jd, b, e); break;
+        default: axpy_groups_exact<K, FLYTE_RTO>(jd, b, e); break;
+      }
+      i0 = e / 4 * 4;
+    }
+  }
+  if (jd.fast == 1) {
     for (int64_t g = b / 4 + threadIdx.x; g < e / 4; g += kBThreads) {
       uint32_t wx[K], wy[K], wo[K];
       load_group<K>(X + g * (4 * K), wx);
@@ -601,6 +645,11 @@ flyte_status make_plan(const flyte_job* jobs, int njobs, Plan& p) {
         d.fast = aligned_to(j.a, group_bytes(j.fx.k)) && aligned_to(j.y, j.fx.base == FLYTE_F64 ? 8 : 4);
       } else if (op == FLYTE_JOB_AXPY) {
         d.fast = j.fx.k == j.fy.k && aligned_to(j.a, group_bytes(j.fy.k)) && aligned_to(j.y, group_bytes(j.fy.k));
+        // alpha a binary32 number inside the window, double-based k = 2..4: the exact binary32 path
+        const float af = float(j.alpha);
+        if (d.fast && j.fy.base == FLYTE_F64 && j.fy.k >= 2 && j.fy.k <= 4 && double(af) == j.alpha &&
+            std::fabs(j.alpha) >= 0x1p-40 && std::fabs(j.alpha) < 0x1p40)
+          d.fast = 2;
       } else {
         // per thread: 4 slots, (step / 4) / threads groups each; block sum (3 + 5 levels) and the tiles
         const int64_t L = step / (4 * kBThreads) + 1;

@@ -27,6 +27,7 @@ class Batch:
         self.host = []
         self.dev = []
         self.jobs = []
+        self.naxpy = 0
         for s in specs:
             op, k, base, n, m = s["op"], s["k"], s["base"], s["n"], s["m"]
             dt = np.float32 if base == 0 else np.float64
@@ -47,8 +48,13 @@ class Batch:
             elif op == 2:
                 h["y"] = oracle.pack(g.standard_normal(n).astype(dt), base, k)
                 d["y"] = self._dev(h["y"], offset)
-                h["alpha"] = float(g.uniform(-2, 2))
-                job = flyte.job(flyte.JOB_AXPY, fx, n, d["x"], d["y"], fy=fx, alpha=h["alpha"], mode="rne")
+                # every other axpy job takes a binary32 alpha (the exact binary32 path for double-based
+                # k <= 4) and the rounding mode cycles through the four
+                self.naxpy += 1
+                a = g.uniform(-2, 2)
+                h["alpha"] = float(np.float32(a)) if self.naxpy % 2 else float(a)
+                h["mode"] = self.naxpy % 4
+                job = flyte.job(flyte.JOB_AXPY, fx, n, d["x"], d["y"], fy=fx, alpha=h["alpha"], mode=h["mode"])
             else:
                 h["A"] = oracle.pack(g.standard_normal(m * n).astype(dt), base, k)
                 lx, ly = (n, m) if op == 3 else (m, n)
@@ -86,7 +92,7 @@ class Batch:
                 assert abs(got - ref) <= 4 * n * EPS * absum + 2 * EPS * abs(ref), s
             elif op == 2 and not skip_axpy:
                 got = d["y"][: n * k].cpu().numpy()
-                want = oracle.axpy(n, h["alpha"], h["x"], (base, k), 1, h["y"], (base, k), 1, oracle.RNE)
+                want = oracle.axpy(n, h["alpha"], h["x"], (base, k), 1, h["y"], (base, k), 1, h["mode"])
                 assert np.array_equal(got, want), s
             elif op >= 3:
                 trans = "N" if op == 3 else "T"
