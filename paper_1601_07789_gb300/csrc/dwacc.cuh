@@ -149,14 +149,15 @@ __device__ __forceinline__ bool dbl_to_pair(uint32_t h, uint32_t l, float& hi, f
   if constexpr (K <= 4) {
     lo = 0.f;
   } else {
-    // remaining bits l[28:0] weigh 2^(e - 1075); keep at most 23 of them
+    // the bits below hi's last one, l[28:0] (at most 23 of them kept), as the
+    // exact difference (Sterbenz) of two binary32 numbers with hi's sign and an
+    // exponent 23 below hi's: one with those bits as its leading fraction bits,
+    // one with fraction 0 (in window the exponent stays normal)
     constexpr int kBits = 8 * (K - 4) - 3;                   // 5, 13, 21, 29
-    constexpr int kSh = kBits > 23 ? 29 - 23 : 29 - kBits;   // shift so they fit 23 bits
-    const uint32_t L = (l & 0x1FFFFFFFu) >> kSh;
-    const float lf = __fsub_rn(__uint_as_float(0x4B000000u | L), 8388608.0f);
-    // scale = sign * 2^(e - 1075 + kSh): exponent field of hi minus (52 - kSh)
-    const uint32_t sb = (hb & 0xFF800000u) - (uint32_t(52 - kSh) << 23);
-    lo = __fmul_rn(lf, __uint_as_float(sb));
+    constexpr int kKeep = kBits > 23 ? 23 : kBits;
+    const uint32_t sbase = (hb & 0xFF800000u) - (23u << 23);
+    const uint32_t frac = ((l & 0x1FFFFFFFu) >> (29 - kKeep)) << (23 - kKeep);
+    lo = __fsub_rn(__uint_as_float(sbase | frac), __uint_as_float(sbase));
   }
   return ok;
 }

@@ -94,10 +94,12 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 //  - 'N' runs the persistent producer/consumer ring below for every k when A
 //    is 16-byte aligned (k = 4: 0.298 -> 0.233 ms, k = 5: 0.377 -> 0.338 ms),
 //    8 consumer warps of 2 rows, 512 columns per stage and two blocks per SM
-//    for k <= 4, 1024 columns per stage and one block per SM for k > 4
-//    (k = 5: 0.338 -> 0.332 ms), tiles of up to 4096 columns (8 warps of 4
-//    rows, 16 warps of 2 rows, 256-column stages were slower); the
-//    direct kernel (2 or 4 groups per lane and step) serves the rest;
+//    for k <= 4; one block per SM for k > 4, with 16 warps of one row and
+//    1024 columns per stage for k = 5, 6 (k = 5: 0.338 -> 0.302 ms) and 12
+//    warps of one row and 512 columns for k = 7, 8; tiles of up to 4096
+//    columns (8 warps of 4 rows, 16 warps of 2 rows, 24 warps of one row,
+//    256-column stages were slower); the direct kernel (2 or 4 groups per
+//    lane and step) serves the rest;
 //  - 'T' loads 4 rows per step and prefetches the next step while folding
 //    the current one.  A producer/consumer ring for 'T' (8 rows per stage)
 //    was not reliably faster (0.208-0.249 ms at k = 4 against 0.222 ms) and
@@ -482,12 +484,27 @@ __global__ void __launch_bounds__(256) gemv_t_finish_packed(const double* __rest
 #ifndef FLYTE_PC_SMEM_LARGE_K
 #define FLYTE_PC_SMEM_LARGE_K 200000   // ring budget per block, k > 4: one block per SM
 #endif
+#ifndef FLYTE_PC_WARPS_LARGE_K
+#define FLYTE_PC_WARPS_LARGE_K 16      // consumer warps per block, k = 5, 6
+#endif
+#ifndef FLYTE_PC_WARPS_K78
+#define FLYTE_PC_WARPS_K78 12          // consumer warps per block, k = 7, 8
+#endif
 
-constexpr int kPcWarps = FLYTE_PC_WARPS;
-constexpr int kPcRows = FLYTE_PC_ROWS;
-constexpr int kPcRowsBlock = kPcWarps * kPcRows;
-constexpr int kPcThreads = (kPcWarps + 1) * 32;
-static_assert(kPcRowsBlock + 2 <= 64, "the producer warp issues at most two copies per lane and stage");
+// k > 4 runs one block per SM; warps of one row hide latency better there
+// than 8 warps of two rows (k = 5: 0.331 -> 0.302 ms with 16 warps, k = 8:
+// 0.387 -> ~0.36 ms with 12), while k <= 4, with two blocks per SM, is faster
+// with 8 warps of two rows (k = 3: 0.256 against 0.282 ms with 16 of one).
+template <int K>
+__host__ __device__ constexpr int pc_warps() {
+  return K <= 4 ? FLYTE_PC_WARPS : (K <= 6 ? FLYTE_PC_WARPS_LARGE_K : FLYTE_PC_WARPS_K78);
+}
+template <int K>
+__host__ __device__ constexpr int pc_rows() { return K <= 4 ? FLYTE_PC_ROWS : 1; }
+template <int K>
+__host__ __device__ constexpr int pc_rows_block() { return pc_warps<K>() * pc_rows<K>(); }
+template <int K>
+__host__ __device__ constexpr int pc_threads() { return (pc_warps<K>() + 1) * 32; }
 
 template <int K>
 __host__ __device__ constexpr int pc_cols() {
@@ -495,7 +512,7 @@ __host__ __device__ constexpr int pc_cols() {
   return K <= 4 ? FLYTE_PC_COLS_SMALL_K : (K <= 6 ? FLYTE_PC_COLS_LARGE_K : 512);
 }
 template <int K>
-__host__ __device__ constexpr int pc_stage_bytes() { return 8 * pc_cols<K>() + kPcRowsBlock * pc_cols<K>() * K; }
+__host__ __device__ constexpr int pc_stage_bytes() { return 8 * pc_cols<K>() + pc_rows_block<K>() * pc_cols<K>() * K; }
 template <int K>
 __host__ __device__ constexpr int pc_stages() {
   constexpr int s = (K <= 4 ? FLYTE_PC_SMEM : FLYTE_PC_SMEM_LARGE_K) / pc_stage_bytes<K>();
@@ -505,7 +522,7 @@ template <int K>
 __host__ __device__ constexpr int pc_smem() { return pc_stages<K>() * pc_stage_bytes<K>() + 16 * pc_stages<K>() + 128; }
 
 template <int BASE, int K, bool LAZY>
-__global__ void __launch_bounds__(kPcThreads) gemv_n_pc(
+__global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
     const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
     const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t chunk_cols,
     int64_t nchunks, double* __restrict__ partial, double alpha, double beta, double* __restrict__ y,
@@ -514,6 +531,11 @@ __global__ void __launch_bounds__(kPcThreads) gemv_n_pc(
   constexpr int S = pc_stages<K>();
   constexpr int kStage = pc_stage_bytes<K>();
   constexpr int kRowBytes = SC * K;
+  constexpr int kPcWarps = pc_warps<K>();
+  constexpr int kPcRows = pc_rows<K>();
+  constexpr int kPcRowsBlock = pc_rows_block<K>();
+  static_assert(kPcRowsBlock + 2 <= 64, "the producer warp issues at most two copies per lane and stage");
+  static_assert(pc_threads<K>() <= 1024, "block too large");
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + S * kStage);
   uint64_t* empty = full + S;
@@ -846,14 +868,15 @@ flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const v
       dim3 grid(unsigned((m + kNRowsPerBlock - 1) / kNRowsPerBlock), unsigned(p.nchunks));
       if (pc) {
         constexpr int smem = pc_smem<K>();
-        const int64_t ntiles = ((m + kPcRowsBlock - 1) / kPcRowsBlock) * p.nchunks;
+        constexpr int rows_block = pc_rows_block<K>(), threads = pc_threads<K>();
+        const int64_t ntiles = ((m + rows_block - 1) / rows_block) * p.nchunks;
         auto run = [&](auto kern) -> flyte_status {
           if (!set_smem_once(kern, smem)) return cuda_status(cudaGetLastError(), "gemv");
           int per_sm = 0;
-          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPcThreads, smem) != cudaSuccess)
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess)
             return cuda_status(cudaGetLastError(), "gemv");
           const int64_t blocks = min(ntiles, int64_t(max(per_sm, 1)) * sm_count());
-          kern<<<unsigned(blocks), kPcThreads, smem, s>>>(A8, lda, m, n, x1, x2, x, incx, p.chunk_cols, p.nchunks,
+          kern<<<unsigned(blocks), threads, smem, s>>>(A8, lda, m, n, x1, x2, x, incx, p.chunk_cols, p.nchunks,
                                                          part, alpha, beta, y, incy, status, direct);
           return FLYTE_OK;
         };
