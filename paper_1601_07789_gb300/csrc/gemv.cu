@@ -100,8 +100,12 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 //    columns (8 warps of 4 rows, 16 warps of 2 rows, 24 warps of one row,
 //    256-column stages were slower); the direct kernel (2 or 4 groups per
 //    lane and step) serves the rest;
-//  - 'T' loads 4 rows per step and prefetches the next step while folding
-//    the current one.  A producer/consumer ring for 'T' (8 rows per stage)
+//  - 'T' loads 8 rows per step without a software prefetch, with registers
+//    capped so that 5 blocks (4 for k = 4) reside per SM (k = 6: 0.312 ->
+//    0.282 ms, k = 4: 0.222 -> 0.202 ms against 4 rows with the next 4
+//    prefetched; 12 or 16 rows, 4 or 6 blocks for other k were slower; with
+//    no cap the compiler used more registers and the kernel ran ~15 % slower).
+//    A producer/consumer ring for 'T' (8 rows per stage)
 //    was not reliably faster (0.208-0.249 ms at k = 4 against 0.222 ms) and
 //    was dropped, as was a warp-private bulk-copy pipeline for both.
 #ifndef FLYTE_N_UNROLL_SMALL_K
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 #define FLYTE_N_UNROLL_LARGE_K 4
 #endif
 #ifndef FLYTE_T_ROWS
-#define FLYTE_T_ROWS 4
+#define FLYTE_T_ROWS 8
 #endif
 #ifndef FLYTE_GEMV_PC
 #define FLYTE_GEMV_PC 1
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 #define FLYTE_GEMV_PREFETCH_N 0
 #endif
 #ifndef FLYTE_GEMV_PREFETCH_T
-#define FLYTE_GEMV_PREFETCH_T 1
+#define FLYTE_GEMV_PREFETCH_T 0
 #endif
 
 constexpr int kNWarps = 8;
@@ -304,6 +308,15 @@ __global__ void __launch_bounds__(256) gemv_n_finish_packed(const double* __rest
 // ---- gemv T ---------------------------------------------------------------------
 
 constexpr int kTThreads = 128;
+// resident blocks per SM that the 'T' kernel's register use must allow
+template <int K>
+constexpr int t_min_blocks() {
+#ifdef FLYTE_T_MIN_BLOCKS
+  return FLYTE_T_MIN_BLOCKS;
+#else
+  return K == 4 ? 4 : 5;
+#endif
+}
 constexpr int kTRowsPerIter = FLYTE_T_ROWS;   // rows loaded per iteration (a multiple of 4)
 
 // Every fold_rows rows the two row-parity chains of each column are
@@ -323,7 +336,7 @@ __device__ __forceinline__ void fold_parities(DW (&acc)[2][4], DW (&tot)[4]) {
 }
 
 template <int BASE, int K, bool LAZY>
-__global__ void __launch_bounds__(kTThreads) gemv_t_kernel(
+__global__ void __launch_bounds__(kTThreads, t_min_blocks<K>()) gemv_t_kernel(
     const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
     const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t rb,
     int64_t fold_rows, double* __restrict__ partial, int fast) {
