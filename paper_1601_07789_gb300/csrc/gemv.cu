@@ -93,13 +93,15 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 // 16384 x 16384, double-based k = 3..6:
 //  - 'N' runs the persistent producer/consumer ring below for every k when A
 //    is 16-byte aligned (k = 4: 0.298 -> 0.233 ms, k = 5: 0.377 -> 0.338 ms),
-//    8 consumer warps of 2 rows, 512 columns per stage and two blocks per SM
-//    for k <= 4; one block per SM for k > 4, with 16 warps of one row and
+//    8 consumer warps of 2 rows, 512 columns per stage and three blocks per
+//    SM for k <= 4 (two stages each; two blocks of up to 113 KiB were 2 %
+//    slower); one block per SM for k > 4, with 16 warps of one row and
 //    1024 columns per stage for k = 5, 6 (k = 5: 0.338 -> 0.302 ms) and 12
 //    warps of one row and 512 columns for k = 7, 8; tiles of up to 4096
 //    columns (8 warps of 4 rows, 16 warps of 2 rows, 24 warps of one row,
-//    256-column stages were slower); the direct kernel (2 or 4 groups per
-//    lane and step) serves the rest;
+//    256-column stages were slower); a full stage's group loop is unrolled
+//    (k = 3: 0.253 -> 0.229 ms, k = 5: 0.302 -> 0.289 ms); the direct kernel
+//    (2 or 4 groups per lane and step) serves the rest;
 //  - 'T' loads 8 rows per step without a software prefetch, with registers
 //    capped so that 5 blocks (4 for k = 4) reside per SM (k = 6: 0.312 ->
 //    0.282 ms, k = 4: 0.222 -> 0.202 ms against 4 rows with the next 4
@@ -492,10 +494,13 @@ __global__ void __launch_bounds__(256) gemv_t_finish_packed(const double* __rest
 #define FLYTE_PC_ROWS 2                // rows per consumer warp
 #endif
 #ifndef FLYTE_PC_SMEM
-#define FLYTE_PC_SMEM 115456           // ring budget per block, k <= 4: two blocks per SM
+#define FLYTE_PC_SMEM 75000            // ring budget per block, k <= 4: three blocks per SM
 #endif
 #ifndef FLYTE_PC_SMEM_LARGE_K
 #define FLYTE_PC_SMEM_LARGE_K 200000   // ring budget per block, k > 4: one block per SM
+#endif
+#ifndef FLYTE_PC_UNROLL_FULL
+#define FLYTE_PC_UNROLL_FULL 1         // unroll the group loop of a full stage
 #endif
 #ifndef FLYTE_PC_WARPS_LARGE_K
 #define FLYTE_PC_WARPS_LARGE_K 16      // consumer warps per block, k = 5, 6
@@ -506,7 +511,7 @@ __global__ void __launch_bounds__(256) gemv_t_finish_packed(const double* __rest
 
 // k > 4 runs one block per SM; warps of one row hide latency better there
 // than 8 warps of two rows (k = 5: 0.331 -> 0.302 ms with 16 warps, k = 8:
-// 0.387 -> ~0.36 ms with 12), while k <= 4, with two blocks per SM, is faster
+// 0.387 -> ~0.36 ms with 12), while k <= 4, with three blocks per SM, is faster
 // with 8 warps of two rows (k = 3: 0.256 against 0.282 ms with 16 of one).
 template <int K>
 __host__ __device__ constexpr int pc_warps() {
@@ -622,7 +627,7 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
       if (!__all_sync(0xFFFFFFFFu, got)) return;   // the producer stops at its next bounded wait
       const uint8_t* d = smem + st * kStage;
       const int cols = int(min(int64_t(SC), cfull - c0));
-      for (int g = lane; g < (cols >> 2); g += 32) {
+      auto group = [&](int g) {
         const float4 xa = reinterpret_cast<const float4*>(d)[g];
         const float4 xb = reinterpret_cast<const float4*>(d + 4 * SC)[g];
         const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
@@ -635,6 +640,13 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
           for (int e = 0; e < 4; ++e)
             fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
         }
+      };
+      if (FLYTE_PC_UNROLL_FULL && cols == SC) {
+        // a full stage: a fixed number of groups per lane, unrolled
+#pragma unroll
+        for (int j = 0; j < SC / 128; ++j) group(lane + 32 * j);
+      } else {
+        for (int g = lane; g < (cols >> 2); g += 32) group(g);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[st]);
