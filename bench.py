@@ -285,6 +285,22 @@ def host_threads() -> int:
         return max(1, os.cpu_count() or 1)
 
 
+def median_ms(fn, stream, reps: int = 20, warmup: int = 3) -> float:
+    """Median over `reps` calls of fn's device time (CUDA events on `stream` around each call), after
+    `warmup` untimed calls."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
 def oracle_sample(rows: int, reps: int = 1, threads: int = 1):
     """Time the oracle on `rows` x 16384 slices of the workload; returns (GB/s, seconds, desc).
 
@@ -428,18 +444,8 @@ def run_flyte(args):
     # native binary64 gemv on the same GPU (cuBLAS through torch) and our own k = 8
     Am = A64.view(M, N)
 
-    def timeit(fn, reps=20):
-        for _ in range(3):
-            fn()
-        torch.cuda.synchronize()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(reps):
-            fn()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        return s0.elapsed_time(s1) / reps
+    def timeit(fn):
+        return median_ms(fn, stream)
 
     yn = torch.empty(M, dtype=torch.float64, device=dev)
     native_ms = {"N": timeit(lambda: torch.mv(Am, x[:N], out=yn)),
@@ -564,25 +570,16 @@ def run_e2e(args, codes, x, y, ws, dev, dist, world):
 
 
 def run_rows(dev, hbm_peak):
-    """Each other hot-path row timed on its own (CUDA events, averages over repetitions)."""
+    """Each other hot-path row timed on its own (CUDA events around each call, median of 20 calls after 3
+    untimed ones)."""
     import torch
 
     from paper_1601_07789_gb300 import flyte
     stream = torch.cuda.current_stream()
     rows = {}
 
-    def timeit(fn, reps=10):
-        for _ in range(3):
-            fn()
-        torch.cuda.synchronize()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(reps):
-            fn()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        return s0.elapsed_time(s1) / reps
+    def timeit(fn):
+        return median_ms(fn, stream)
 
     def entry(nbytes, ms, flops=None):
         d = {"ms": round(ms, 4), "GBps": round(nbytes / (ms * 1e-3) / 1e9, 1),
@@ -635,18 +632,9 @@ def run_gemm_rows(dev):
     out = {}
 
     def timeit(fn, reps):
-        fn()
-        torch.cuda.synchronize()
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(reps):
-            fn()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        return s0.elapsed_time(s1) / reps
+        return median_ms(fn, stream, reps=reps)
 
-    for k, size, reps in ((2, 8192, 5), (3, 8192, 3), (4, 8192, 3), (5, 4096, 2)):
+    for k, size, reps in ((2, 8192, 20), (3, 8192, 20), (4, 8192, 20), (5, 4096, 20)):
         base = 0 if k <= 4 else 1
         f = (k, base)
         dt = torch.float32 if base == 0 else torch.float64

@@ -706,10 +706,37 @@ __global__ void scale_y(double* __restrict__ y, int64_t len, int64_t incy, doubl
     y[j * incy] = beta == 0.0 ? 0.0 : beta * y[j * incy];
 }
 
-#ifndef FLYTE_T_ROW_TILE
-#define FLYTE_T_ROW_TILE 128
+// Row tile of gemv T: a multiple of 16 rows in [96, 160], chosen per call so
+// that the grid (column blocks x row tiles) fills its last wave of resident
+// blocks well: the smallest (waves rounded up) x (rows per tile), ties to the
+// larger tile (fewer partial sums).  At 16384 x 16384 fixed tiles measured
+// 144 rows (4.8 waves) 1-2.5 % faster than 128 (5.4 waves), 136 (5.1) the
+// slowest; allowing up to 256 rows picked 176 there (1 % slower than 144)
+// and 208 at 12288 x 12288 (1 % slower than the 144 chosen within 160).
+// Defining FLYTE_T_ROW_TILE fixes the tile instead.
+#ifndef FLYTE_T_ROW_TILE_MAX
+#define FLYTE_T_ROW_TILE_MAX 160
 #endif
-constexpr int64_t kTRowTile = FLYTE_T_ROW_TILE;   // row tile of gemv T
+constexpr int64_t kTRowTileMin = 96, kTRowTileMax = FLYTE_T_ROW_TILE_MAX;
+
+int64_t t_row_tile(int64_t m, int64_t n, int64_t resident) {
+#ifdef FLYTE_T_ROW_TILE
+  (void)m, (void)n, (void)resident;
+  return FLYTE_T_ROW_TILE;
+#else
+  const int64_t cb = (n + 4 * kTThreads - 1) / (4 * kTThreads);
+  int64_t best = kTRowTileMin, best_cost = -1;
+  for (int64_t rb = kTRowTileMin; rb <= kTRowTileMax; rb += 16) {
+    const int64_t blocks = cb * ((m + rb - 1) / rb);
+    const int64_t cost = (blocks + resident - 1) / max(resident, int64_t(1)) * rb;
+    if (best_cost < 0 || cost <= best_cost) {
+      best_cost = cost;
+      best = rb;
+    }
+  }
+  return best;
+#endif
+}
 
 int64_t align16(int64_t b) { return (b + 15) & ~int64_t(15); }
 
@@ -727,7 +754,9 @@ struct Plan {
   int64_t off_status, off_x1, off_x2, off_part, bytes;
 };
 
-Plan plan_gemv(char trans, int64_t m, int64_t n) {
+// rb: the 'T' row tile; 0 sizes the plan for the smallest tile (the most
+// partial sums), which is what the workspace query reports.
+Plan plan_gemv(char trans, int64_t m, int64_t n, int64_t rb = 0) {
   Plan p{};
   const int64_t lenx = trans == 'N' ? n : m;
   p.off_status = 0;                   // int: error bits of the bulk-copy pipeline
@@ -759,7 +788,11 @@ Plan plan_gemv(char trans, int64_t m, int64_t n) {
     }
     p.bytes = p.off_part + 8 * m * p.nchunks;   // partial sums (also for one chunk with a packed y)
   } else {
-    p.rb = kTRowTile;
+#ifdef FLYTE_T_ROW_TILE
+    p.rb = FLYTE_T_ROW_TILE;
+#else
+    p.rb = rb > 0 ? rb : kTRowTileMin;
+#endif
     p.ntiles = (m + p.rb - 1) / p.rb;
     // chain: fold_rows / 2 rows per parity (+ up to kTRowsPerIter trailing
     // rows); double-word: the parity sum and one total per fold (the folds of
@@ -859,7 +892,7 @@ flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const v
       return FLYTE_OK;
     });
   }
-  const Plan p = plan_gemv(trans, m, n);
+  Plan p = plan_gemv(trans, m, n);
   if (ws == nullptr || ws_bytes < size_t(p.bytes)) {
     set_error("gemv: workspace of %lld bytes required", (long long)p.bytes);
     return FLYTE_ERR_WORKSPACE;
@@ -878,6 +911,14 @@ flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const v
   const int direct = (trans == 'N' && p.nchunks == 1 && ky == 0) ? 1 : 0;
   double* y = static_cast<double*>(yv);
   const flyte_status st = dispatch_fmt(fa, [&]<int BASE, int K>() -> flyte_status {
+    if (trans == 'T') {
+      // the row tile for this grid and the kernel's occupancy (no more partial sums than sized for)
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemv_t_kernel<BASE, K, true>, kTThreads, 0) !=
+          cudaSuccess)
+        return cuda_status(cudaGetLastError(), "gemv");
+      p = plan_gemv(trans, m, n, t_row_tile(m, n, int64_t(max(per_sm, 1)) * sm_count()));
+    }
     constexpr int S = group_bytes(K);
     const bool aligned = reinterpret_cast<uintptr_t>(A) % S == 0 && (lda * K) % S == 0;
     const int fast = (p.fast && aligned) ? 1 : 0;

@@ -65,7 +65,7 @@ def test_gemv_static_matches_workspace_path_twice(trans, m, n, k):
 
 
 def test_gemv_static_rejects_calls_beyond_its_scratch():
-    m = n = 16384                                   # 'T' needs ~16.5 MB of scratch
+    m = n = 16384                                   # 'T' needs ~22 MB of scratch
     assert flyte.workspace_bytes("gemv_t", m, n, 0, (4, 1)) > 4 << 20
     y = torch.zeros(8, dtype=torch.float64, device="cuda")
     with pytest.raises(flyte.FlyteError) as e:
