@@ -95,7 +95,7 @@ def run_case(args):
         for _ in range(2):
             flyte.dot(xs, (k, 1), ys, (k, 1))
             flyte.axpy(1.5, xs, (k, 1), ys, (k, 1))      # binary32 alpha: the exact binary32 path
-            flyte.axpy(1e-9, xs, (k, 1), ys, (k, 1))     # any other alpha: binary64 fma
+            flyte.axpy(0.1, xs, (k, 1), ys, (k, 1))      # any other alpha: two binary32 parts
     elif args.case == "batch":
         from paper_1601_07789_gb300 import inputs
         specs = inputs.batch_specs(512, seed=5)
@@ -606,7 +606,8 @@ def run_rows(dev, hbm_peak):
     rows["dot_f64_k4"] = entry(2 * 4 * n, timeit(lambda: flyte.dot(xs, (4, 1), ys, (4, 1), n=n, out=res, ws=wsd)),
                                2 * n)
     rows["axpy_f64_k4"] = entry(3 * 4 * n, timeit(lambda: flyte.axpy(1.5, xs, (4, 1), ys, (4, 1), n=n)), 2 * n)
-    rows["axpy_f64_k4_alpha_not_binary32"] = entry(3 * 4 * n, timeit(lambda: flyte.axpy(1e-9 + 1e-25, xs, (4, 1), ys, (4, 1), n=n)), 2 * n)
+    # alpha = 0.1 is not a binary32 number: the two-part binary32 path
+    rows["axpy_f64_k4_alpha_not_binary32"] = entry(3 * 4 * n, timeit(lambda: flyte.axpy(0.1, xs, (4, 1), ys, (4, 1), n=n)), 2 * n)
     rows["n"] = n
     del v, out, xs, ys
     rows.update(run_gemm_rows(dev))

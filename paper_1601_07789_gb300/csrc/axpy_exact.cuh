@@ -18,7 +18,10 @@
 // can differ from s only by 2^-27 u_h, so it cannot move s across a boundary
 // unless s lies within that distance of it; such elements (|w| <= 2^-20 u_h,
 // not exactly on the boundary), exact zeros and anything outside the window
-// send their group to the binary64 FMA instead.
+// send their group to the binary64 FMA instead.  Any other binary64 alpha in
+// the window is split into two binary32 parts (axpy_exact_f32x2 below): the
+// same chain with one more product, and a guard widened by a bound on the few
+// terms it leaves out.
 #pragma once
 
 #include "dwacc.cuh"
@@ -32,29 +35,22 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
+// The code of pack(RN64(s)) for s = h + l + t2 + r, where h + l + t2 comes from the TwoSum chain
+// below and |r| <= margin (margin = 0: s = h + l + t2 exactly, and a result exactly on a rounding
+// boundary is decided too).  False sends the element to the binary64 path.
 template <int K, int MODE>
-__device__ __forceinline__ bool axpy_exact_f32(uint64_t ux, uint64_t uy, float af, uint64_t& code) {
+__device__ __forceinline__ bool axpy_decide(float h, float l, float t2, float margin, uint64_t& code) {
   constexpr int m = 8 * K - 12;          // mantissa bits of the code
   constexpr int d = 23 - m;              // bits of h below the code's last bit
   constexpr bool kNearest = MODE == FLYTE_RNE || MODE == FLYTE_HALF_UP;
   constexpr float kB = kNearest ? float(1u << (d - 1)) : 0.f;   // boundary, in ulps of h
-  float xf, yf, unused;
-  bool ok = dbl_to_pair<K>(uint32_t(ux >> 32), 0u, xf, unused);
-  ok &= dbl_to_pair<K>(uint32_t(uy >> 32), 0u, yf, unused);
-  const float p = __fmul_rn(af, xf);
-  const float e = __fmaf_rn(af, xf, -p);
-  float s1, t1, s2, t2, h, l;
-  two_sum(p, yf, s1, t1);
-  two_sum(t1, e, s2, t2);
-  two_sum(s1, s2, h, l);
-  // s = h + l + t2 exactly.  t2 != 0 needs p + y inexact, hence no cancellation in it, so
-  // |t2| <= 2^-24 ulp(s1) and |l + t2| <= ulp(h) / 2 + tiny: L = RN(l + t2) errs by at most
-  // 2^-24 ulp(h), far inside the 2^-20 ulp(h) guard below; the exact error is formed only when a
-  // decision falls on a boundary.
+  // t2 != 0 needs p + y inexact, hence no cancellation in it, so |t2| <= 2^-23 ulp(s1) and
+  // |l + t2| <= ulp(h) / 2 + tiny: L = RN(l + t2) errs by at most 2^-23 ulp(h), far inside the
+  // 2^-20 ulp(h) guard below; the exact error is formed only when a decision falls on a boundary.
   const float L = __fadd_rn(l, t2);
   const uint32_t hb = __float_as_uint(h);
   const uint32_t E = (hb >> 23) & 0xFFu;
-  ok &= E >= 24u;                        // zero or too small for the exact code path: binary64
+  bool ok = E >= 24u;                    // zero or too small for the exact code path: binary64
   const uint32_t M = hb & 0x7FFFFFu;
   const uint32_t D = M & ((1u << d) - 1u);
   const uint64_t Q = (uint64_t(E + 896u) << m) | (M >> d);
@@ -64,11 +60,11 @@ __device__ __forceinline__ bool axpy_exact_f32(uint64_t ux, uint64_t uy, float a
   const float z = __fmul_rn(__fsub_rn(Df, kB), uh);                            // (D - B) u_h exactly
   const float w = __fadd_rn(z, neg ? -L : L);
   int sg = (w > 0.f) - (w < 0.f);                                              // sign of f - B
-  if (!(fabsf(w) > __fmul_rn(uh, 0x1p-20f))) {
-    // within the guard: decided only if exactly on the boundary
+  if (!(fabsf(w) > __fmaf_rn(uh, 0x1p-20f, margin))) {
+    // within the guard: decided only if s is known exactly and on the boundary
     float L2, Le;
     two_sum(l, t2, L2, Le);
-    ok &= w == 0.f && Le == 0.f;
+    ok &= margin == 0.f && w == 0.f && Le == 0.f;
     sg = 0;
   }
   uint64_t q;
@@ -85,5 +81,42 @@ __device__ __forceinline__ bool axpy_exact_f32(uint64_t ux, uint64_t uy, float a
   return ok;
 }
 
+// alpha a binary32 number af: s = p + e + y exactly.
+template <int K, int MODE>
+__device__ __forceinline__ bool axpy_exact_f32(uint64_t ux, uint64_t uy, float af, uint64_t& code) {
+  float xf, yf, unused;
+  bool ok = dbl_to_pair<K>(uint32_t(ux >> 32), 0u, xf, unused);
+  ok &= dbl_to_pair<K>(uint32_t(uy >> 32), 0u, yf, unused);
+  const float p = __fmul_rn(af, xf);
+  const float e = __fmaf_rn(af, xf, -p);
+  float s1, t1, s2, t2, h, l;
+  two_sum(p, yf, s1, t1);
+  two_sum(t1, e, s2, t2);
+  two_sum(s1, s2, h, l);
+  return axpy_decide<K, MODE>(h, l, t2, 0.f, code) && ok;
+}
+
+// Any binary64 alpha inside the window, split on the host as a1 = RN32(alpha),
+// a2 = RN32(alpha - a1) (alpha - a1 - a2 = a3 with |a3| <= 2^-24 |a2|).  With
+// p + e1 = a1 x (TwoProd), p2 = RN(a2 x) and eA + eB = e1 + p2 (TwoSum), the
+// chain of the binary32 case runs on p, y and eA; the terms left out, eB,
+// a2 x - p2 and a3 x, are each at most about 2^-47 |p|, so |r| <= 2^-45 |p|
+// bounds them, and a decision is taken only outside the guard widened by it.
+template <int K, int MODE>
+__device__ __forceinline__ bool axpy_exact_f32x2(uint64_t ux, uint64_t uy, float a1, float a2, uint64_t& code) {
+  float xf, yf, unused;
+  bool ok = dbl_to_pair<K>(uint32_t(ux >> 32), 0u, xf, unused);
+  ok &= dbl_to_pair<K>(uint32_t(uy >> 32), 0u, yf, unused);
+  const float p = __fmul_rn(a1, xf);
+  const float e1 = __fmaf_rn(a1, xf, -p);
+  const float p2 = __fmul_rn(a2, xf);
+  float eA, eB;
+  two_sum(e1, p2, eA, eB);
+  float s1, t1, s2, t2, h, l;
+  two_sum(p, yf, s1, t1);
+  two_sum(t1, eA, s2, t2);
+  two_sum(s1, s2, h, l);
+  return axpy_decide<K, MODE>(h, l, t2, __fmul_rn(fabsf(p), 0x1p-45f), code) && ok;
+}
 
 }  // namespace flyte

@@ -176,13 +176,15 @@ __device__ __forceinline__ uint64_t axpy_elem(typename Native<BASE>::bits ux, ty
   }
 }
 
-// Groups [b/4, e/4) with the exact binary32 element of axpy_exact.cuh (alpha a binary32 number,
-// double-based k <= 4; the host sets fast = 2), binary64 for a group that needs it.
-template <int K, int MODE>
+// Groups [b/4, e/4) with the exact binary32 elements of axpy_exact.cuh (double-based k <= 4, alpha
+// in the window; the host sets fast = 2 when alpha is a binary32 number, 3 otherwise), binary64 for
+// a group that needs it.
+template <int K, int MODE, bool SPLIT>
 __device__ void axpy_groups_exact(const JobDev& jd, int64_t b, int64_t e) {
   const uint8_t* X = static_cast<const uint8_t*>(jd.j.a);
   uint8_t* Y = static_cast<uint8_t*>(jd.j.y);
   const float af = __double2float_rn(jd.j.alpha);
+  const float a2 = __double2float_rn(jd.j.alpha - double(af));
   for (int64_t g = b / 4 + threadIdx.x; g < e / 4; g += kBThreads) {
     uint32_t wx[K], wy[K], wo[K];
     load_group<K>(X + g * (4 * K), wx);
@@ -192,9 +194,14 @@ __device__ void axpy_groups_exact(const JobDev& jd, int64_t b, int64_t e) {
     uint64_t c[4];
     bool ok = true;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      ok &= axpy_exact_f32<K, MODE>(extract_widened<FLYTE_F64, K>(wx, q), extract_widened<FLYTE_F64, K>(wy, q), af,
-                                    c[q]);
+    for (int q = 0; q < 4; ++q) {
+      const uint64_t ux = extract_widened<FLYTE_F64, K>(wx, q), uy = extract_widened<FLYTE_F64, K>(wy, q);
+      if constexpr (SPLIT) {
+        ok &= axpy_exact_f32x2<K, MODE>(ux, uy, af, a2, c[q]);
+      } else {
+        ok &= axpy_exact_f32<K, MODE>(ux, uy, af, c[q]);
+      }
+    }
     if (!ok) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
@@ -219,10 +226,18 @@ __device__ void axpy_tile(const JobDev& jd, int64_t b, int64_t e) {
   if constexpr (BASE == FLYTE_F64 && K >= 2 && K <= 4) {
     if (jd.fast == 2) {
       switch (jd.j.mode) {
-        case FLYTE_RNE: axpy_groups_exact<K, FLYTE_RNE>(jd, b, e); break;
-        case FLYTE_RTZ: axpy_groups_exact<K, FLYTE_RTZ>(jd, b, e); break;
-        case FLYTE_HALF_UP: axpy_groups_exact<K, FLYTE_HALF_UP>(jd, b, e); break;
-        default: axpy_groups_exact<K, FLYTE_RTO>(jd, b, e); break;
+        case FLYTE_RNE: axpy_groups_exact<K, FLYTE_RNE, false>(jd, b, e); break;
+        case FLYTE_RTZ: axpy_groups_exact<K, FLYTE_RTZ, false>(jd, b, e); break;
+        case FLYTE_HALF_UP: axpy_groups_exact<K, FLYTE_HALF_UP, false>(jd, b, e); break;
+        default: axpy_groups_exact<K, FLYTE_RTO, false>(jd, b, e); break;
+      }
+      i0 = e / 4 * 4;
+    } else if (jd.fast == 3) {
+      switch (jd.j.mode) {
+        case FLYTE_RNE: axpy_groups_exact<K, FLYTE_RNE, true>(jd, b, e); break;
+        case FLYTE_RTZ: axpy_groups_exact<K, FLYTE_RTZ, true>(jd, b, e); break;
+        case FLYTE_HALF_UP: axpy_groups_exact<K, FLYTE_HALF_UP, true>(jd, b, e); break;
+        default: axpy_groups_exact<K, FLYTE_RTO, true>(jd, b, e); break;
       }
       i0 = e / 4 * 4;
     }
@@ -645,11 +660,11 @@ flyte_status make_plan(const flyte_job* jobs, int njobs, Plan& p) {
         d.fast = aligned_to(j.a, group_bytes(j.fx.k)) && aligned_to(j.y, j.fx.base == FLYTE_F64 ? 8 : 4);
       } else if (op == FLYTE_JOB_AXPY) {
         d.fast = j.fx.k == j.fy.k && aligned_to(j.a, group_bytes(j.fy.k)) && aligned_to(j.y, group_bytes(j.fy.k));
-        // alpha a binary32 number inside the window, double-based k = 2..4: the exact binary32 path
-        const float af = float(j.alpha);
-        if (d.fast && j.fy.base == FLYTE_F64 && j.fy.k >= 2 && j.fy.k <= 4 && double(af) == j.alpha &&
-            std::fabs(j.alpha) >= 0x1p-40 && std::fabs(j.alpha) < 0x1p40)
-          d.fast = 2;
+        // alpha inside the window, double-based k = 2..4: the exact binary32 paths (2: alpha is a
+        // binary32 number, 3: two binary32 parts)
+        if (d.fast && j.fy.base == FLYTE_F64 && j.fy.k >= 2 && j.fy.k <= 4 && std::fabs(j.alpha) >= 0x1p-40 &&
+            std::fabs(j.alpha) < 0x1p40)
+          d.fast = double(float(j.alpha)) == j.alpha ? 2 : 3;
       } else {
         // per thread: 4 slots, (step / 4) / threads groups each; block sum (3 + 5 levels) and the tiles
         const int64_t L = step / (4 * kBThreads) + 1;

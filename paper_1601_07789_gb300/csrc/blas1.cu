@@ -168,11 +168,13 @@ __global__ void __launch_bounds__(kThreads) axpy_groups(const uint8_t* __restric
 
 // ---- axpy without binary64 arithmetic: axpy_exact.cuh ------------------------------------
 
-template <int K, int MODE>
+// SPLIT = false: alpha is a binary32 number; true: any alpha in the window, as two binary32 parts.
+template <int K, int MODE, bool SPLIT>
 __global__ void __launch_bounds__(kThreads) axpy_groups_f32exact(const uint8_t* __restrict__ X,
                                                                  uint8_t* __restrict__ Y, int64_t ngrp,
                                                                  double alpha) {
   const float af = float(alpha);
+  const float a2 = float(alpha - double(af));
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngrp; g += stride) {
     uint32_t wx[K], wy[K], wo[K];
@@ -183,9 +185,14 @@ __global__ void __launch_bounds__(kThreads) axpy_groups_f32exact(const uint8_t* 
     uint64_t c[4];
     bool ok = true;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      ok &= axpy_exact_f32<K, MODE>(extract_widened<FLYTE_F64, K>(wx, q), extract_widened<FLYTE_F64, K>(wy, q), af,
-                                    c[q]);
+    for (int q = 0; q < 4; ++q) {
+      const uint64_t ux = extract_widened<FLYTE_F64, K>(wx, q), uy = extract_widened<FLYTE_F64, K>(wy, q);
+      if constexpr (SPLIT) {
+        ok &= axpy_exact_f32x2<K, MODE>(ux, uy, af, a2, c[q]);
+      } else {
+        ok &= axpy_exact_f32<K, MODE>(ux, uy, af, c[q]);
+      }
+    }
     if (!ok) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
@@ -198,14 +205,16 @@ __global__ void __launch_bounds__(kThreads) axpy_groups_f32exact(const uint8_t* 
   }
 }
 
-template <int K>
+template <int K, bool SPLIT>
 void launch_axpy_f32exact(const uint8_t* X, uint8_t* Y, int64_t ngrp, double alpha, int mode, cudaStream_t s) {
   const unsigned grid = grid_for(ngrp, kThreads);
   switch (mode) {
-    case FLYTE_RNE: axpy_groups_f32exact<K, FLYTE_RNE><<<grid, kThreads, 0, s>>>(X, Y, ngrp, alpha); break;
-    case FLYTE_RTZ: axpy_groups_f32exact<K, FLYTE_RTZ><<<grid, kThreads, 0, s>>>(X, Y, ngrp, alpha); break;
-    case FLYTE_HALF_UP: axpy_groups_f32exact<K, FLYTE_HALF_UP><<<grid, kThreads, 0, s>>>(X, Y, ngrp, alpha); break;
-    default: axpy_groups_f32exact<K, FLYTE_RTO><<<grid, kThreads, 0, s>>>(X, Y, ngrp, alpha); break;
+    case FLYTE_RNE: axpy_groups_f32exact<K, FLYTE_RNE, SPLIT><<<grid, kThreads, 0, s>>>(X, Y, ngrp, alpha); break;
+    case FLYTE_RTZ: axpy_groups_f32exact<K, FLYTE_RTZ, SPLIT><<<grid, kThreads, 0, s>>>(X, Y, ngrp, alpha); break;
+    case FLYTE_HALF_UP:
+      axpy_groups_f32exact<K, FLYTE_HALF_UP, SPLIT><<<grid, kThreads, 0, s>>>(X, Y, ngrp, alpha);
+      break;
+    default: axpy_groups_f32exact<K, FLYTE_RTO, SPLIT><<<grid, kThreads, 0, s>>>(X, Y, ngrp, alpha); break;
   }
 }
 
@@ -330,10 +339,13 @@ flyte_status launch_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, i
       const int64_t ngrp = n / 4;
       bool done = false;
       if constexpr (BASE == FLYTE_F64 && KY >= 2 && KY <= 4) {
-        // alpha a binary32 number inside the window: the exact binary32 path
-        const float af = float(alpha);
-        if (double(af) == alpha && std::fabs(alpha) >= 0x1p-40 && std::fabs(alpha) < 0x1p40) {
-          launch_axpy_f32exact<KY>(X, Y, ngrp, alpha, mode, s);
+        // alpha inside the window: the exact binary32 paths (one part when alpha is a binary32 number)
+        if (std::fabs(alpha) >= 0x1p-40 && std::fabs(alpha) < 0x1p40) {
+          if (double(float(alpha)) == alpha) {
+            launch_axpy_f32exact<KY, false>(X, Y, ngrp, alpha, mode, s);
+          } else {
+            launch_axpy_f32exact<KY, true>(X, Y, ngrp, alpha, mode, s);
+          }
           done = true;
         }
       }

@@ -96,8 +96,9 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 //    8 consumer warps of 2 rows, 512 columns per stage and three blocks per
 //    SM for k <= 4 (two stages each; two blocks of up to 113 KiB were 2 %
 //    slower); one block per SM for k > 4, with 16 warps of one row and
-//    1024 columns per stage for k = 5, 6 (k = 5: 0.338 -> 0.302 ms) and 12
-//    warps of one row and 512 columns for k = 7, 8; tiles of up to 4096
+//    1024 columns per stage for k = 5, 6 (k = 5: 0.338 -> 0.302 ms); 12
+//    warps of one row, 512 columns and two blocks per SM for k = 7, 8 (k = 8:
+//    0.355 -> 0.335 ms against one block); tiles of up to 4096
 //    columns (8 warps of 4 rows, 16 warps of 2 rows, 24 warps of one row,
 //    256-column stages were slower); a full stage's group loop is unrolled
 //    (k = 3: 0.253 -> 0.229 ms, k = 5: 0.302 -> 0.289 ms); the direct kernel
@@ -497,7 +498,10 @@ __global__ void __launch_bounds__(256) gemv_t_finish_packed(const double* __rest
 #define FLYTE_PC_SMEM 75000            // ring budget per block, k <= 4: three blocks per SM
 #endif
 #ifndef FLYTE_PC_SMEM_LARGE_K
-#define FLYTE_PC_SMEM_LARGE_K 200000   // ring budget per block, k > 4: one block per SM
+#define FLYTE_PC_SMEM_LARGE_K 200000   // ring budget per block, k = 5, 6: one block per SM
+#endif
+#ifndef FLYTE_PC_SMEM_K78
+#define FLYTE_PC_SMEM_K78 110000       // ring budget per block, k = 7, 8: two blocks per SM
 #endif
 #ifndef FLYTE_PC_UNROLL_FULL
 #define FLYTE_PC_UNROLL_FULL 1         // unroll the group loop of a full stage
@@ -533,7 +537,7 @@ template <int K>
 __host__ __device__ constexpr int pc_stage_bytes() { return 8 * pc_cols<K>() + pc_rows_block<K>() * pc_cols<K>() * K; }
 template <int K>
 __host__ __device__ constexpr int pc_stages() {
-  constexpr int s = (K <= 4 ? FLYTE_PC_SMEM : FLYTE_PC_SMEM_LARGE_K) / pc_stage_bytes<K>();
+  constexpr int s = (K <= 4 ? FLYTE_PC_SMEM : (K <= 6 ? FLYTE_PC_SMEM_LARGE_K : FLYTE_PC_SMEM_K78)) / pc_stage_bytes<K>();
   return s < 2 ? 2 : (s > 8 ? 8 : s);
 }
 template <int K>

@@ -273,3 +273,33 @@ def test_axpy_binary32_alpha_exact_path(k, mode):
     for alpha in (1.5, 0.5, 3.0):
         got = run_axpy(n, alpha, xi, f, 1, yi, f, 1, mode)
         check_axpy(got, n, alpha, xi, f, 1, yi, f, 1, mode)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("mode", MODES)
+def test_axpy_split_alpha_exact_path(k, mode):
+    """Any other alpha inside the window takes the two-part binary32 path for double-based k <= 4:
+    bit-exact against the oracle, with near-cancellations (y close to -alpha x), zeros, small
+    integers and out-of-window values mixed in."""
+    f = (k, 1)
+    g = np.random.default_rng(60 + k)
+    n = 1 << 16
+    xv = g.standard_normal(n)
+    yv = g.standard_normal(n)
+    yv[1::11] = 0.0
+    xv[2::13] *= 2.0 ** g.integers(-60, 60, xv[2::13].size)
+    alphas = (0.1, -1e-9 - 1e-25, np.pi, 1.0 / 3.0, 1.5 + 2.0 ** -30, -1.1 * 2.0 ** -39, 123456.789,
+              float(g.uniform(-4, 4)), float(g.uniform(-4, 4)) * 2.0 ** 30)
+    xs = _stream(xv, f)
+    for alpha in alphas:
+        assert float(np.float32(alpha)) != alpha
+        yc = yv.copy()
+        yc[::7] = -alpha * xv[::7]          # near-cancellation: y is alpha x rounded to the format
+        ys = _stream(yc, f)
+        got = run_axpy(n, alpha, xs, f, 1, ys, f, 1, mode)
+        check_axpy(got, n, alpha, xs, f, 1, ys, f, 1, mode)
+    xi = _stream(g.integers(-64, 64, n).astype(np.float64), f)
+    yi = _stream(g.integers(-4096, 4096, n).astype(np.float64) * 0.5, f)
+    for alpha in (0.1, 1.0 / 3.0, 0.5 + 2.0 ** -40):
+        got = run_axpy(n, alpha, xi, f, 1, yi, f, 1, mode)
+        check_axpy(got, n, alpha, xi, f, 1, yi, f, 1, mode)
