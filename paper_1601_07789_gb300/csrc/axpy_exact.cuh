@@ -35,11 +35,17 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
   t = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
+// The parts of the product left out of the chain when alpha is split (a2, a3 and the products'
+// pieces), used only for a decision that falls on a rounding boundary.
+struct SplitRest {
+  float a2, a3, xf, p, p2, eB;
+};
+
 // The code of pack(RN64(s)) for s = h + l + t2 + r, where h + l + t2 comes from the TwoSum chain
-// below and |r| <= margin (margin = 0: s = h + l + t2 exactly, and a result exactly on a rounding
-// boundary is decided too).  False sends the element to the binary64 path.
-template <int K, int MODE>
-__device__ __forceinline__ bool axpy_decide(float h, float l, float t2, float margin, uint64_t& code) {
+// below and |r| <= margin (SPLIT = false: r = 0).  False sends the element to the binary64 path.
+template <int K, int MODE, bool SPLIT>
+__device__ __forceinline__ bool axpy_decide(float h, float l, float t2, float margin, const SplitRest& rest,
+                                            uint64_t& code) {
   constexpr int m = 8 * K - 12;          // mantissa bits of the code
   constexpr int d = 23 - m;              // bits of h below the code's last bit
   constexpr bool kNearest = MODE == FLYTE_RNE || MODE == FLYTE_HALF_UP;
@@ -55,17 +61,40 @@ __device__ __forceinline__ bool axpy_decide(float h, float l, float t2, float ma
   const uint32_t D = M & ((1u << d) - 1u);
   const uint64_t Q = (uint64_t(E + 896u) << m) | (M >> d);
   const float uh = __uint_as_float(max(E, 24u) - 23u << 23);
+  // r must stay below u_h / 4, so that s stays within the boundaries next to h: heavy
+  // cancellation (|alpha x| above ~2^20 |s|) goes to binary64
+  ok &= margin < __fmul_rn(uh, 0.25f);
   const bool neg = hb >> 31;
   const float Df = __fsub_rn(__uint_as_float(0x4B000000u | D), 8388608.0f);   // D exactly
   const float z = __fmul_rn(__fsub_rn(Df, kB), uh);                            // (D - B) u_h exactly
   const float w = __fadd_rn(z, neg ? -L : L);
   int sg = (w > 0.f) - (w < 0.f);                                              // sign of f - B
   if (!(fabsf(w) > __fmaf_rn(uh, 0x1p-20f, margin))) {
-    // within the guard: decided only if s is known exactly and on the boundary
+    // Near a boundary.  Here |w| < u_h / 4 forces z = 0 or a cancellation, so w = z + L exactly,
+    // and s lies F = w + Le + r (oriented like w) above the boundary, with Le the error of L and
+    // r the terms left out of the chain.  The boundary lies within 0.6 u_h of h, so in h's binade
+    // (or, when h is a power of two, at h itself), where half a binary64 ulp is hu = 2^-53 2^e(h)
+    // (hu / 2 just below a power of two).  The binary64 fma rounds s onto the boundary when |F| is
+    // below that and strictly to the side of F when |F| is above hu; at hu binary64 decides.
     float L2, Le;
     two_sum(l, t2, L2, Le);
-    ok &= margin == 0.f && w == 0.f && Le == 0.f;
-    sg = 0;
+    float rc = 0.f, re = 0.f;                  // r within re (SPLIT = false: r = 0)
+    if constexpr (SPLIT) {
+      // r = eB + (a2 x - p2) + a3 x + (less than 2^-70 |p|)
+      const float e2 = __fmaf_rn(rest.a2, rest.xf, -rest.p2);
+      const float p3 = __fmul_rn(rest.a3, rest.xf);
+      rc = __fadd_rn(__fadd_rn(rest.eB, e2), p3);
+      const float sa = __fadd_rn(__fadd_rn(fabsf(rest.eB), fabsf(e2)), fabsf(p3));
+      re = __fadd_rn(__fmaf_rn(sa, 0x1p-22f, __fmul_rn(fabsf(rest.p), 0x1p-66f)), 0x1p-126f);
+    }
+    const float F = __fadd_rn(__fadd_rn(w, neg ? -Le : Le), neg ? -rc : rc);
+    const float eF = __fmaf_rn(__fadd_rn(__fadd_rn(fabsf(w), fabsf(Le)), fabsf(rc)), 0x1p-23f, re);
+    const float hu = __uint_as_float(max(E, 54u) - 53u << 23);
+    const bool exact = F == 0.f && eF == 0.f;                  // exactly on the boundary
+    const bool snap = __fadd_rn(fabsf(F), eF) < (M == 0u ? __fmul_rn(hu, 0.5f) : hu);
+    const bool beyond = __fsub_rn(fabsf(F), eF) > hu;
+    ok &= exact || (E >= 100u && fabsf(w) < __fmul_rn(uh, 0.25f) && (snap || beyond));
+    sg = exact || snap ? 0 : (F > 0.f ? 1 : -1);
   }
   uint64_t q;
   if constexpr (MODE == FLYTE_RNE) {
@@ -93,17 +122,18 @@ __device__ __forceinline__ bool axpy_exact_f32(uint64_t ux, uint64_t uy, float a
   two_sum(p, yf, s1, t1);
   two_sum(t1, e, s2, t2);
   two_sum(s1, s2, h, l);
-  return axpy_decide<K, MODE>(h, l, t2, 0.f, code) && ok;
+  return axpy_decide<K, MODE, false>(h, l, t2, 0.f, SplitRest{}, code) && ok;
 }
 
-// Any binary64 alpha inside the window, split on the host as a1 = RN32(alpha),
-// a2 = RN32(alpha - a1) (alpha - a1 - a2 = a3 with |a3| <= 2^-24 |a2|).  With
-// p + e1 = a1 x (TwoProd), p2 = RN(a2 x) and eA + eB = e1 + p2 (TwoSum), the
-// chain of the binary32 case runs on p, y and eA; the terms left out, eB,
-// a2 x - p2 and a3 x, are each at most about 2^-47 |p|, so |r| <= 2^-45 |p|
-// bounds them, and a decision is taken only outside the guard widened by it.
+// Any binary64 alpha inside the window, split as a1 = RN32(alpha), a2 = RN32(alpha - a1),
+// a3 = RN32(alpha - a1 - a2) (|alpha - a1 - a2 - a3| <= 2^-72 |alpha|).  With p + e1 = a1 x
+// (TwoProd), p2 = RN(a2 x) and eA + eB = e1 + p2 (TwoSum), the chain of the binary32 case runs on
+// p, y and eA; the terms left out, eB, a2 x - p2 and (alpha - a1 - a2) x, are each at most about
+// 2^-47 |p|, so |r| <= 2^-45 |p| bounds them, and a decision away from a boundary is taken only
+// outside the guard widened by it.
 template <int K, int MODE>
-__device__ __forceinline__ bool axpy_exact_f32x2(uint64_t ux, uint64_t uy, float a1, float a2, uint64_t& code) {
+__device__ __forceinline__ bool axpy_exact_f32x2(uint64_t ux, uint64_t uy, float a1, float a2, float a3,
+                                                 uint64_t& code) {
   float xf, yf, unused;
   bool ok = dbl_to_pair<K>(uint32_t(ux >> 32), 0u, xf, unused);
   ok &= dbl_to_pair<K>(uint32_t(uy >> 32), 0u, yf, unused);
@@ -116,7 +146,9 @@ __device__ __forceinline__ bool axpy_exact_f32x2(uint64_t ux, uint64_t uy, float
   two_sum(p, yf, s1, t1);
   two_sum(t1, eA, s2, t2);
   two_sum(s1, s2, h, l);
-  return axpy_decide<K, MODE>(h, l, t2, __fmul_rn(fabsf(p), 0x1p-45f), code) && ok;
+  return axpy_decide<K, MODE, true>(h, l, t2, __fmul_rn(fabsf(p), 0x1p-45f), SplitRest{a2, a3, xf, p, p2, eB},
+                                    code) &&
+         ok;
 }
 
 }  // namespace flyte

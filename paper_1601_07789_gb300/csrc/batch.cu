@@ -185,6 +185,7 @@ __device__ void axpy_groups_exact(const JobDev& jd, int64_t b, int64_t e) {
   uint8_t* Y = static_cast<uint8_t*>(jd.j.y);
   const float af = __double2float_rn(jd.j.alpha);
   const float a2 = __double2float_rn(jd.j.alpha - double(af));
+  const float a3 = __double2float_rn(jd.j.alpha - double(af) - double(a2));
   for (int64_t g = b / 4 + threadIdx.x; g < e / 4; g += kBThreads) {
     uint32_t wx[K], wy[K], wo[K];
     load_group<K>(X + g * (4 * K), wx);
@@ -197,7 +198,7 @@ __device__ void axpy_groups_exact(const JobDev& jd, int64_t b, int64_t e) {
     for (int q = 0; q < 4; ++q) {
       const uint64_t ux = extract_widened<FLYTE_F64, K>(wx, q), uy = extract_widened<FLYTE_F64, K>(wy, q);
       if constexpr (SPLIT) {
-        ok &= axpy_exact_f32x2<K, MODE>(ux, uy, af, a2, c[q]);
+        ok &= axpy_exact_f32x2<K, MODE>(ux, uy, af, a2, a3, c[q]);
       } else {
         ok &= axpy_exact_f32<K, MODE>(ux, uy, af, c[q]);
       }

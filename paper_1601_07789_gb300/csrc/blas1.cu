@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(kThreads) axpy_groups_f32exact(const uint8_t* 
                                                                  double alpha) {
   const float af = float(alpha);
   const float a2 = float(alpha - double(af));
+  const float a3 = float(alpha - double(af) - double(a2));
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngrp; g += stride) {
     uint32_t wx[K], wy[K], wo[K];
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) axpy_groups_f32exact(const uint8_t* 
     for (int q = 0; q < 4; ++q) {
       const uint64_t ux = extract_widened<FLYTE_F64, K>(wx, q), uy = extract_widened<FLYTE_F64, K>(wy, q);
       if constexpr (SPLIT) {
-        ok &= axpy_exact_f32x2<K, MODE>(ux, uy, af, a2, c[q]);
+        ok &= axpy_exact_f32x2<K, MODE>(ux, uy, af, a2, a3, c[q]);
       } else {
         ok &= axpy_exact_f32<K, MODE>(ux, uy, af, c[q]);
       }
