@@ -70,31 +70,35 @@ __device__ __forceinline__ bool axpy_decide(float h, float l, float t2, float ma
   const float w = __fadd_rn(z, neg ? -L : L);
   int sg = (w > 0.f) - (w < 0.f);                                              // sign of f - B
   if (!(fabsf(w) > __fmaf_rn(uh, 0x1p-20f, margin))) {
-    // Near a boundary.  Here |w| < u_h / 4 forces z = 0 or a cancellation, so w = z + L exactly,
-    // and s lies F = w + Le + r (oriented like w) above the boundary, with Le the error of L and
-    // r the terms left out of the chain.  The boundary lies within 0.6 u_h of h, so in h's binade
-    // (or, when h is a power of two, at h itself), where half a binary64 ulp is hu = 2^-53 2^e(h)
-    // (hu / 2 just below a power of two).  The binary64 fma rounds s onto the boundary when |F| is
-    // below that and strictly to the side of F when |F| is above hu; at hu binary64 decides.
     float L2, Le;
     two_sum(l, t2, L2, Le);
-    float rc = 0.f, re = 0.f;                  // r within re (SPLIT = false: r = 0)
-    if constexpr (SPLIT) {
-      // r = eB + (a2 x - p2) + a3 x + (less than 2^-70 |p|)
+    if constexpr (!SPLIT) {
+      // s = h + l + t2 exactly: decided only when exactly on the boundary (these elements are
+      // frequent with short x, y and a binary32 alpha, so this branch stays short)
+      ok &= w == 0.f && Le == 0.f;
+      sg = 0;
+    } else {
+      // Here |w| < u_h / 4 forces z = 0 or a cancellation, so w = z + L exactly, and s lies
+      // F = w + Le + r (oriented like w) above the boundary, with Le the error of L and r the
+      // terms left out of the chain.  The boundary lies within 0.6 u_h of h, so in h's binade
+      // (or, when h is a power of two, at h itself), where half a binary64 ulp is
+      // hu = 2^-53 2^e(h) (hu / 2 just below a power of two).  The binary64 fma rounds s onto
+      // the boundary when |F| is below that and strictly to the side of F when |F| is above hu;
+      // at hu binary64 decides.  r = eB + (a2 x - p2) + a3 x + (less than 2^-70 |p|), formed
+      // as rc within re.
       const float e2 = __fmaf_rn(rest.a2, rest.xf, -rest.p2);
       const float p3 = __fmul_rn(rest.a3, rest.xf);
-      rc = __fadd_rn(__fadd_rn(rest.eB, e2), p3);
+      const float rc = __fadd_rn(__fadd_rn(rest.eB, e2), p3);
       const float sa = __fadd_rn(__fadd_rn(fabsf(rest.eB), fabsf(e2)), fabsf(p3));
-      re = __fadd_rn(__fmaf_rn(sa, 0x1p-22f, __fmul_rn(fabsf(rest.p), 0x1p-66f)), 0x1p-126f);
+      const float re = __fadd_rn(__fmaf_rn(sa, 0x1p-22f, __fmul_rn(fabsf(rest.p), 0x1p-66f)), 0x1p-126f);
+      const float F = __fadd_rn(__fadd_rn(w, neg ? -Le : Le), neg ? -rc : rc);
+      const float eF = __fmaf_rn(__fadd_rn(__fadd_rn(fabsf(w), fabsf(Le)), fabsf(rc)), 0x1p-23f, re);
+      const float hu = __uint_as_float(max(E, 54u) - 53u << 23);
+      const bool snap = __fadd_rn(fabsf(F), eF) < (M == 0u ? __fmul_rn(hu, 0.5f) : hu);
+      const bool beyond = __fsub_rn(fabsf(F), eF) > hu;
+      ok &= E >= 100u && fabsf(w) < __fmul_rn(uh, 0.25f) && (snap || beyond);
+      sg = snap ? 0 : (F > 0.f ? 1 : -1);
     }
-    const float F = __fadd_rn(__fadd_rn(w, neg ? -Le : Le), neg ? -rc : rc);
-    const float eF = __fmaf_rn(__fadd_rn(__fadd_rn(fabsf(w), fabsf(Le)), fabsf(rc)), 0x1p-23f, re);
-    const float hu = __uint_as_float(max(E, 54u) - 53u << 23);
-    const bool exact = F == 0.f && eF == 0.f;                  // exactly on the boundary
-    const bool snap = __fadd_rn(fabsf(F), eF) < (M == 0u ? __fmul_rn(hu, 0.5f) : hu);
-    const bool beyond = __fsub_rn(fabsf(F), eF) > hu;
-    ok &= exact || (E >= 100u && fabsf(w) < __fmul_rn(uh, 0.25f) && (snap || beyond));
-    sg = exact || snap ? 0 : (F > 0.f ? 1 : -1);
   }
   uint64_t q;
   if constexpr (MODE == FLYTE_RNE) {
