@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "axpy_exact.cuh"
+#include "load_unaligned.cuh"
 #include "dwacc.cuh"
 
 namespace flyte {
@@ -48,6 +49,8 @@ struct JobDev {
   int32_t fold_rows;                          // gemv 'T'
   int32_t row_chunks;                         // gemv 'T': row chunks per column block
   int32_t done_base;                          // first completion counter of the job
+  int32_t ua;                                 // dot/gemv: groups not 4k-byte aligned (funnel-shift loads)
+  int32_t pad;
 };
 
 struct Header {
@@ -138,6 +141,15 @@ __device__ __forceinline__ bool pieces(typename Native<BASE>::bits u, float& hi,
     hi = __uint_as_float(u);
     lo = 0.f;
     return flt_in_window(u);
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void load_group_any(const uint8_t* p, uint32_t (&w)[K], int ua) {
+  if (ua) {
+    load_group_unaligned<K>(p, w);
+  } else {
+    load_group<K>(p, w);
   }
 }
 
@@ -281,8 +293,8 @@ __device__ double dot_share(const JobDev& jd, int64_t b, int64_t e) {
   if (jd.fast) {
     for (int64_t g = b / 4 + threadIdx.x; g < e / 4; g += kBThreads) {
       uint32_t wx[K], wy[K];
-      load_group<K>(X + g * (4 * K), wx);
-      load_group<K>(Y + g * (4 * K), wy);
+      load_group_any<K>(X + g * (4 * K), wx, jd.ua);
+      load_group_any<K>(Y + g * (4 * K), wy, jd.ua);
       typename Native<BASE>::bits ux[4], uy[4];
       bool ok = true;
       float p[4], s[4];
@@ -381,7 +393,7 @@ __device__ void gemv_n_tile(const JobDev& jd, int64_t r0, int64_t r1, float* x1,
       bool ok = true;
       for (int64_t g = lane; g < n / 4; g += 32) {
         uint32_t w[K];
-        load_group<K>(Ar + g * (4 * K), w);
+        load_group_any<K>(Ar + g * (4 * K), w, jd.ua);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           fold_elem<BASE, K>(extract_widened<BASE, K>(w, q), x1[4 * g + q], x2[4 * g + q], acc[q], ok);
@@ -436,7 +448,7 @@ __device__ void gemv_t_tile(const JobDev& jd, int tile, int64_t r0, int64_t r1, 
     int since = 0;
     for (int64_t i = r0; i < r1; ++i) {
       uint32_t w[K];
-      load_group<K>(colp + i * n * K, w);
+      load_group_any<K>(colp + i * n * K, w, jd.ua);
       const float a1 = x1[i - r0], a2 = x2[i - r0];
 #pragma unroll
       for (int q = 0; q < 4; ++q) fold_elem<BASE, K>(extract_widened<BASE, K>(w, q), a1, a2, acc[i & 1][q], ok);
@@ -621,12 +633,13 @@ flyte_status make_plan(const flyte_job* jobs, int njobs, Plan& p) {
     if (op == FLYTE_JOB_GEMV_N || op == FLYTE_JOB_GEMV_T) {
       if (j.m == 0 || j.n == 0) continue;
       const int K = j.fx.k;
-      const bool al = aligned_to(j.a, group_bytes(K)) && (j.n * K) % group_bytes(K) == 0;
+      // rows whose groups are not 4k-byte aligned are read with funnel-shift loads
+      d.ua = !(aligned_to(j.a, group_bytes(K)) && (j.n * K) % group_bytes(K) == 0);
       if (op == FLYTE_JOB_GEMV_N) {
         // chains of n/128 + 1 terms per slot; then a double-word tree (2 + 5 levels, one binary64
         // step) or, for rows too short for its bound, binary64 (3 + 5 levels)
         const int64_t L = j.n / 128 + 2;
-        d.fast = !al ? 0 : (dw_bound_ok(j.n, L, 1, 14, 7) ? 1 : (dw_bound_ok(j.n, L, 9, 14) ? 2 : 0));
+        d.fast = dw_bound_ok(j.n, L, 1, 14, 7) ? 1 : (dw_bound_ok(j.n, L, 9, 14) ? 2 : 0);
         add_items(j.m, tile);
       } else {
         // tiles: 1024-column blocks x chunks of `tile` rows; parity chains of fold/2 + 1 terms folded
@@ -636,7 +649,7 @@ flyte_status make_plan(const flyte_job* jobs, int njobs, Plan& p) {
         const int64_t ncb = (j.n + 4 * kBThreads - 1) / (4 * kBThreads);
         d.fast = 0;
         d.fold_rows = 64;
-        for (int64_t f = 64; f >= 2 && al; f /= 2) {
+        for (int64_t f = 64; f >= 2; f /= 2) {
           if (dw_bound_ok(j.m, f / 2 + 1, 2 * (rows / f) + 4 + nrc, 14)) {
             d.fast = 1;
             d.fold_rows = int32_t(f);
@@ -670,8 +683,8 @@ flyte_status make_plan(const flyte_job* jobs, int njobs, Plan& p) {
         // per thread: 4 slots, (step / 4) / threads groups each; block sum (3 + 5 levels) and the tiles
         const int64_t L = step / (4 * kBThreads) + 1;
         const int64_t tiles = (j.n + step - 1) / step;
-        d.fast = j.fx.k == j.fy.k && j.fx.base == j.fy.base && aligned_to(j.a, group_bytes(j.fx.k)) &&
-                 aligned_to(j.y, group_bytes(j.fx.k)) && dw_bound_ok(j.n, L, 4 + 8 + tiles + 1, 20);
+        d.fast = j.fx.k == j.fy.k && j.fx.base == j.fy.base && dw_bound_ok(j.n, L, 4 + 8 + tiles + 1, 20);
+        d.ua = !(aligned_to(j.a, group_bytes(j.fx.k)) && aligned_to(j.y, group_bytes(j.fx.k)));
       }
       add_items(j.n, step);
       if (op == FLYTE_JOB_DOT) {

@@ -20,6 +20,7 @@
 #include <cmath>
 
 #include "axpy_exact.cuh"
+#include "load_unaligned.cuh"
 #include "dwacc.cuh"
 
 namespace flyte {
@@ -49,7 +50,8 @@ __device__ __forceinline__ double bits_to_double(typename Native<BASE>::bits u) 
   }
 }
 
-template <int BASE, int K>
+// UA: x or y not 4k-byte aligned (groups read with load_group_unaligned).
+template <int BASE, int K, bool UA>
 __global__ void __launch_bounds__(kThreads) dot_groups(const uint8_t* __restrict__ X, const uint8_t* __restrict__ Y,
                                                        int64_t ngrp, int64_t n, int fast,
                                                        double* __restrict__ partial) {
@@ -62,8 +64,13 @@ __global__ void __launch_bounds__(kThreads) dot_groups(const uint8_t* __restrict
   const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   for (int64_t g = tid; g < ngrp; g += stride) {
     uint32_t wx[K], wy[K];
-    load_group<K>(X + g * (4 * K), wx);
-    load_group<K>(Y + g * (4 * K), wy);
+    if constexpr (UA) {
+      load_group_unaligned<K>(X + g * (4 * K), wx);
+      load_group_unaligned<K>(Y + g * (4 * K), wy);
+    } else {
+      load_group<K>(X + g * (4 * K), wx);
+      load_group<K>(Y + g * (4 * K), wy);
+    }
     typename Native<BASE>::bits ux[4], uy[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -306,7 +313,9 @@ flyte_status launch_dot(double* result, int64_t n, const void* x, flyte_fmt fx, 
   const uint8_t* Y = static_cast<const uint8_t*>(y);
   const bool same = fx.k == fy.k && fx.base == fy.base;
   const int S = group_bytes(fx.k);
-  const bool groups = same && incx == 1 && incy == 1 && aligned(x, S) && aligned(y, S) && n >= 4;
+  // unit strides and one format: 4-element groups (funnel-shift loads when a stream is not 4k-byte aligned)
+  const bool groups = same && incx == 1 && incy == 1 && n >= 4;
+  const bool ua = !(aligned(x, S) && aligned(y, S));
   int nblocks;
   if (groups) {
     const int64_t ngrp = n / 4;
@@ -314,7 +323,11 @@ flyte_status launch_dot(double* result, int64_t n, const void* x, flyte_fmt fx, 
     const int64_t L = (ngrp + int64_t(nblocks) * kThreads - 1) / (int64_t(nblocks) * kThreads);
     const int fast = dw_bound_ok(n, L, 4 + 5 + 7 + (nblocks + kThreads - 1) / kThreads + 12, 20) ? 1 : 0;
     flyte_status st = dispatch_fmt(fx, [&]<int BASE, int K>() -> flyte_status {
-      dot_groups<BASE, K><<<nblocks, kThreads, 0, s>>>(X, Y, ngrp, n, fast, partial);
+      if (ua) {
+        dot_groups<BASE, K, true><<<nblocks, kThreads, 0, s>>>(X, Y, ngrp, n, fast, partial);
+      } else {
+        dot_groups<BASE, K, false><<<nblocks, kThreads, 0, s>>>(X, Y, ngrp, n, fast, partial);
+      }
       FLYTE_TRY_LAUNCH("dot");
       return FLYTE_OK;
     });

@@ -23,6 +23,7 @@
 // group, tile) of 'T' is recomputed with binary64 FMAs over the raw bytes.
 #include "bulkpipe.cuh"
 #include "dwacc.cuh"
+#include "load_unaligned.cuh"
 
 namespace flyte {
 namespace {
@@ -152,7 +153,17 @@ constexpr int64_t kNChunkCols = FLYTE_PC_CHUNK;   // columns per chunk, a multip
 template <int K>
 __host__ __device__ constexpr int n_unroll() { return K <= 4 ? FLYTE_N_UNROLL_SMALL_K : FLYTE_N_UNROLL_LARGE_K; }
 
-template <int BASE, int K, bool LAZY>
+// A group of A: vector loads, or (UA: rows not 4k-byte aligned) funnel-shift loads.
+template <int K, bool UA>
+__device__ __forceinline__ void load_grp(const uint8_t* p, uint32_t (&w)[K]) {
+  if constexpr (UA) {
+    load_group_unaligned<K>(p, w);
+  } else {
+    load_group<K>(p, w);
+  }
+}
+
+template <int BASE, int K, bool LAZY, bool UA>
 __global__ void __launch_bounds__(kNWarps * 32) gemv_n_kernel(
     const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
     const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t chunk_cols,
@@ -189,7 +200,7 @@ __global__ void __launch_bounds__(kNWarps * 32) gemv_n_kernel(
         xa[u] = __ldg(reinterpret_cast<const float4*>(x1) + gu);
         xb[u] = __ldg(reinterpret_cast<const float4*>(x2) + gu);
 #pragma unroll
-        for (int r = 0; r < kNRowsPerWarp; ++r) load_group<K>(rowp[r] + gu * (4 * K), w[u][r]);
+        for (int r = 0; r < kNRowsPerWarp; ++r) load_grp<K, UA>(rowp[r] + gu * (4 * K), w[u][r]);
       }
     };
 #if FLYTE_GEMV_PREFETCH_N
@@ -233,7 +244,7 @@ __global__ void __launch_bounds__(kNWarps * 32) gemv_n_kernel(
 #pragma unroll
       for (int r = 0; r < kNRowsPerWarp; ++r) {
         uint32_t w[K];
-        load_group<K>(rowp[r] + g * (4 * K), w);
+        load_grp<K, UA>(rowp[r] + g * (4 * K), w);
 #pragma unroll
         for (int e = 0; e < 4; ++e)
           fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
@@ -338,7 +349,7 @@ __device__ __forceinline__ void fold_parities(DW (&acc)[2][4], DW (&tot)[4]) {
   }
 }
 
-template <int BASE, int K, bool LAZY>
+template <int BASE, int K, bool LAZY, bool UA>
 __global__ void __launch_bounds__(kTThreads, t_min_blocks<K>()) gemv_t_kernel(
     const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
     const float* __restrict__ x2, const double* __restrict__ x, int64_t incx, int64_t rb,
@@ -371,7 +382,7 @@ __global__ void __launch_bounds__(kTThreads, t_min_blocks<K>()) gemv_t_kernel(
         b2[u] = q.x; b2[u + 1] = q.y; b2[u + 2] = q.z; b2[u + 3] = q.w;
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) load_group<K>(colp + (r + u) * lda * K, w[u]);
+      for (int u = 0; u < U; ++u) load_grp<K, UA>(colp + (r + u) * lda * K, w[u]);
     };
 #if FLYTE_GEMV_PREFETCH_T
     // software pipeline: the next batch of rows is in flight while this one is folded
@@ -407,7 +418,7 @@ __global__ void __launch_bounds__(kTThreads, t_min_blocks<K>()) gemv_t_kernel(
     }
     for (; i < i1; ++i) {
       uint32_t w[K];
-      load_group<K>(colp + i * lda * K, w);
+      load_grp<K, UA>(colp + i * lda * K, w);
       const float a1 = x1[i], a2 = x2[i];
 #pragma unroll
       for (int e = 0; e < 4; ++e) fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), a1, a2, acc[0][e], ok);
@@ -918,21 +929,22 @@ flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const v
     if (trans == 'T') {
       // the row tile for this grid and the kernel's occupancy (no more partial sums than sized for)
       int per_sm = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemv_t_kernel<BASE, K, true>, kTThreads, 0) !=
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemv_t_kernel<BASE, K, true, false>, kTThreads, 0) !=
           cudaSuccess)
         return cuda_status(cudaGetLastError(), "gemv");
       p = plan_gemv(trans, m, n, t_row_tile(m, n, int64_t(max(per_sm, 1)) * sm_count()));
     }
     constexpr int S = group_bytes(K);
-    const bool aligned = reinterpret_cast<uintptr_t>(A) % S == 0 && (lda * K) % S == 0;
-    const int fast = (p.fast && aligned) ? 1 : 0;
+    // rows whose groups are not 4k-byte aligned take the funnel-shift loads (UA kernels)
+    const bool ua = !(reinterpret_cast<uintptr_t>(A) % S == 0 && (lda * K) % S == 0);
+    const int fast = p.fast ? 1 : 0;
     if (fast) {
       prep_x<<<grid_for(lenx, 256), 256, 0, s>>>(x, lenx, incx, x1, x2, status);
       FLYTE_TRY_LAUNCH("gemv");
     }
     const uint8_t* A8 = static_cast<const uint8_t*>(A);
     // the producer's bulk copies need A and every row start 16-byte aligned
-    const bool pc = FLYTE_GEMV_PC && K <= FLYTE_GEMV_PC_KMAX && fast && reinterpret_cast<uintptr_t>(A) % 16 == 0 &&
+    const bool pc = FLYTE_GEMV_PC && K <= FLYTE_GEMV_PC_KMAX && fast && !ua && reinterpret_cast<uintptr_t>(A) % 16 == 0 &&
                     (lda * K) % 16 == 0;
     if (trans == 'N') {
       dim3 grid(unsigned((m + kNRowsPerBlock - 1) / kNRowsPerBlock), unsigned(p.nchunks));
@@ -952,24 +964,27 @@ flyte_status launch_gemv(char trans, int64_t m, int64_t n, double alpha, const v
         };
         const flyte_status st = p.lazy ? run(gemv_n_pc<BASE, K, true>) : run(gemv_n_pc<BASE, K, false>);
         if (st != FLYTE_OK) return st;
-      } else if (p.lazy) {
-        gemv_n_kernel<BASE, K, true><<<grid, kNWarps * 32, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.chunk_cols,
-                                                                   p.nchunks, part, alpha, beta, y, incy, fast,
-                                                                   direct);
       } else {
-        gemv_n_kernel<BASE, K, false><<<grid, kNWarps * 32, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.chunk_cols,
-                                                                    p.nchunks, part, alpha, beta, y, incy, fast,
-                                                                    direct);
+        auto run = [&](auto kern) {
+          kern<<<grid, kNWarps * 32, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.chunk_cols, p.nchunks, part, alpha,
+                                             beta, y, incy, fast, direct);
+        };
+        if (ua) {
+          p.lazy ? run(gemv_n_kernel<BASE, K, true, true>) : run(gemv_n_kernel<BASE, K, false, true>);
+        } else {
+          p.lazy ? run(gemv_n_kernel<BASE, K, true, false>) : run(gemv_n_kernel<BASE, K, false, false>);
+        }
       }
       FLYTE_TRY_LAUNCH("gemv");
     } else {
       dim3 grid(unsigned((n + 4 * kTThreads - 1) / (4 * kTThreads)), unsigned(p.ntiles));
-      if (p.lazy) {
-        gemv_t_kernel<BASE, K, true><<<grid, kTThreads, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.rb, p.fold_rows,
-                                                                part, fast);
+      auto run = [&](auto kern) {
+        kern<<<grid, kTThreads, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.rb, p.fold_rows, part, fast);
+      };
+      if (ua) {
+        p.lazy ? run(gemv_t_kernel<BASE, K, true, true>) : run(gemv_t_kernel<BASE, K, false, true>);
       } else {
-        gemv_t_kernel<BASE, K, false><<<grid, kTThreads, 0, s>>>(A8, lda, m, n, x1, x2, x, incx, p.rb,
-                                                                 p.fold_rows, part, fast);
+        p.lazy ? run(gemv_t_kernel<BASE, K, true, false>) : run(gemv_t_kernel<BASE, K, false, false>);
       }
       FLYTE_TRY_LAUNCH("gemv");
     }
