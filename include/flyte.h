@@ -22,7 +22,10 @@
  *    errors return FLYTE_ERR_CUDA.  flyte_last_error_string() describes the
  *    last failure of the calling thread.
  *  - Any pointer alignment is accepted; 16-byte aligned pointers (and, for
- *    matrices, rows that start on 16-byte boundaries) take the fast paths.
+ *    matrices, rows that start on 16-byte boundaries) take the fastest
+ *    paths.  dot and gemv keep their double-word arithmetic for any
+ *    alignment (unaligned 4-element groups are assembled from aligned word
+ *    loads); pack, unpack, axpy and scal fall back to per-element code.
  *  - Outputs must not overlap inputs, except y in flyte_axpy and x in
  *    flyte_scal, which are updated in place.
  */
