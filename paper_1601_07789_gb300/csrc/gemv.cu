@@ -450,15 +450,32 @@ __global__ void __launch_bounds__(kTThreads, t_min_blocks<K>()) gemv_t_kernel(
 
 // Column sums over the tiles: lane = column, warps take tiles w, w+8, ...;
 // the 8 warp sums are added in warp order, so the result is deterministic.
+// Sum of column j over the tiles warp, warp + 8, ... in that order; four loads are issued before
+// their additions so that the column's reads overlap (the order, hence the result, is unchanged).
+__device__ __forceinline__ double tile_column_sum(const double* __restrict__ partial, int64_t ntiles, int64_t n,
+                                                  int64_t j, int warp) {
+  double t = 0.0;
+  if (j >= n) return t;
+  int64_t s = warp;
+  for (; s + 24 < ntiles; s += 32) {
+    const double a0 = partial[s * n + j], a1 = partial[(s + 8) * n + j];
+    const double a2 = partial[(s + 16) * n + j], a3 = partial[(s + 24) * n + j];
+    t += a0;
+    t += a1;
+    t += a2;
+    t += a3;
+  }
+  for (; s < ntiles; s += 8) t += partial[s * n + j];
+  return t;
+}
+
 __global__ void __launch_bounds__(256) gemv_t_finish(const double* __restrict__ partial, int64_t ntiles, int64_t n,
                                                      double alpha, double beta, double* __restrict__ y,
                                                      int64_t incy) {
   __shared__ double red[8][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t j = int64_t(blockIdx.x) * 32 + lane;
-  double t = 0.0;
-  if (j < n)
-    for (int64_t s = warp; s < ntiles; s += 8) t += partial[s * n + j];
+  const double t = tile_column_sum(partial, ntiles, n, j, warp);
   red[warp][lane] = t;
   __syncthreads();
   if (warp == 0 && j < n) {
@@ -475,9 +492,7 @@ __global__ void __launch_bounds__(256) gemv_t_finish_packed(const double* __rest
   __shared__ double red[8][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t j = int64_t(blockIdx.x) * 32 + lane;
-  double t = 0.0;
-  if (j < n)
-    for (int64_t s = warp; s < ntiles; s += 8) t += partial[s * n + j];
+  const double t = tile_column_sum(partial, ntiles, n, j, warp);
   red[warp][lane] = t;
   __syncthreads();
   if (warp == 0 && j < n) {
