@@ -175,6 +175,68 @@ def test_pack_half_up_is_fig6(base, k):
     assert [int(c) for c in got] == fig6
 
 
+# ---- k = 1: rounding in bit-pattern order, found by search ----------------------
+# A one-byte code keeps the sign and the top 7 exponent bits only (the "top k
+# bytes" reading of Sec. 3.1 / Table 1), so its 128 magnitudes are the patterns
+# c << d (d = W - 8).  Nearest, ties, Fig. 6 and round to odd are taken in that
+# pattern order, and the magnitude saturates at 0x7F: there is no Inf or NaN
+# code.  The search below looks the neighbours up in the list of all 128
+# patterns; it shares nothing with the oracle's shift-and-compare.
+
+def _k1_by_search(base: int, u: int, mode: str) -> int:
+    import bisect
+    W = 32 if base == 0 else 64
+    d = W - 8
+    sign = u >> (W - 1)
+    mag = u & ((1 << (W - 1)) - 1)
+    exp_all_ones = (0xFF << 23) if base == 0 else (0x7FF << 52)
+    if mag & exp_all_ones == exp_all_ones:           # Inf or NaN: no such code at k = 1
+        return (sign << 7) | 0x7F
+    patterns = [c << d for c in range(128)]          # every magnitude a code can hold
+    lo = bisect.bisect_right(patterns, mag) - 1      # largest pattern <= mag
+    if patterns[lo] == mag:
+        c = lo
+    elif mode == "rtz":
+        c = lo
+    elif mode == "rto":
+        c = lo if lo % 2 == 1 else lo + 1           # the odd one of the two neighbours
+    elif lo == 127:
+        c = 127                                      # beyond the largest code: saturate
+    else:
+        below, above = mag - patterns[lo], patterns[lo + 1] - mag
+        if below < above:
+            c = lo
+        elif below > above:
+            c = lo + 1
+        elif mode == "half":
+            c = lo + 1
+        else:
+            c = lo if lo % 2 == 0 else lo + 1
+    return (sign << 7) | c
+
+
+def _k1_samples(base: int) -> list[int]:
+    W = 32 if base == 0 else 64
+    d = W - 8
+    h = 1 << (d - 1)
+    drops = [0, 1, h - 1, h, h + 1, 2 * h - 1, h // 3, h + h // 5]
+    out = [(top << d) | r for top in range(256) for r in drops]
+    g = np.random.default_rng(1234 + base)
+    out += [int(v) for v in g.integers(0, 1 << (W - 1), size=3000, dtype=np.uint64)]
+    out += [int(v) | (1 << (W - 1)) for v in g.integers(0, 1 << (W - 1), size=1000, dtype=np.uint64)]
+    return out
+
+
+@pytest.mark.parametrize("base", [0, 1])
+@pytest.mark.parametrize("mode", ["rne", "rtz", "rto", "half"])
+def test_pack_k1_matches_pattern_order_search(base, mode):
+    """Every top byte with ties at even and odd kept parts, near-ties, Inf/NaN and random patterns."""
+    u = np.array(_k1_samples(base), dtype=np.uint32 if base == 0 else np.uint64)
+    got = _codes_from_stream(oracle.pack(u, base, 1, MODES[mode]), 1)
+    for ui, c in zip(u, got):
+        assert int(c) == _k1_by_search(base, int(ui), mode), (hex(int(ui)), mode)
+
+
 # ---- round trip, exhaustive over small widths ----------------------------------
 
 @pytest.mark.parametrize("base,k", [(0, 1), (0, 2), (0, 3), (1, 1), (1, 2)])
