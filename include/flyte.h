@@ -28,6 +28,14 @@
  *    loads); pack, unpack, axpy and scal fall back to per-element code.
  *  - Outputs must not overlap inputs, except y in flyte_axpy and x in
  *    flyte_scal, which are updated in place.
+ *  - Kernels that stream through shared-memory copy rings (gemv 'N', gemm)
+ *    bound every wait (200 ms).  A wait that gives up (a stalled copy
+ *    engine; it does not happen in normal operation) sets the call's status
+ *    word nonzero -- the first 4 bytes of its workspace, which the call
+ *    resets to 0 -- and the outputs the call could not compute are written
+ *    as NaN, so the failure is visible in the results too (for
+ *    flyte_gemv_static, whose status word lies inside the library, only
+ *    there).
  */
 #ifndef FLYTE_H
 #define FLYTE_H

@@ -29,6 +29,19 @@ flyte_status cuda_status(cudaError_t e, const char* what) {
   return FLYTE_ERR_CUDA;
 }
 
+flyte_status check_gemv_args(char trans, int64_t m, int64_t n, double alpha, const void* A, flyte_fmt fa,
+                             int64_t lda, const double* x, int64_t incx, const void* y, int64_t incy) {
+  if (trans != 'N' && trans != 'T' && trans != 'n' && trans != 't') return invalid("trans must be 'N' or 'T'");
+  if (!valid_fmt(fa)) return invalid("format (k, base)");
+  if (m < 0 || n < 0) return invalid("m < 0 or n < 0");
+  if (lda < (n > 1 ? n : 1)) return invalid("lda < max(1, n)");
+  if (incx < 1 || incy < 1) return invalid("stride < 1");
+  if (m == 0 || n == 0) return FLYTE_OK;
+  if (!y) return invalid("null y");
+  if (alpha != 0.0 && (!A || !x)) return invalid("null A or x");
+  return FLYTE_OK;
+}
+
 int sm_count() {
   static thread_local int cached_dev = -1, cached = 0;
   int dev = 0;
@@ -119,16 +132,9 @@ flyte_status flyte_gemv(char trans, int64_t m, int64_t n, double alpha, const vo
                         int64_t lda, const double* x, int64_t incx, double beta, double* y,
                         int64_t incy, void* ws, size_t ws_bytes, cudaStream_t stream) {
   g_error[0] = 0;
-  if (trans == 'n') trans = 'N';
-  if (trans == 't') trans = 'T';
-  if (trans != 'N' && trans != 'T') return invalid("trans must be 'N' or 'T'");
-  if (!valid_fmt(fa)) return invalid("format (k, base)");
-  if (m < 0 || n < 0) return invalid("m < 0 or n < 0");
-  if (lda < (n > 1 ? n : 1)) return invalid("lda < max(1, n)");
-  if (incx < 1 || incy < 1) return invalid("stride < 1");
-  if (m == 0 || n == 0) return FLYTE_OK;
-  if (!y) return invalid("null y");
-  if (alpha != 0.0 && (!A || !x)) return invalid("null A or x");
+  const flyte_status st = check_gemv_args(trans, m, n, alpha, A, fa, lda, x, incx, y, incy);
+  if (st != FLYTE_OK || m == 0 || n == 0) return st;
+  trans = (trans == 'n' || trans == 'N') ? 'N' : 'T';
   return launch_gemv(trans, m, n, alpha, A, fa, lda, x, incx, beta, y, 0, incy, 0, ws, ws_bytes, stream);
 }
 

@@ -15,6 +15,10 @@ namespace flyte {
 
 void set_error(const char* fmt, ...);
 flyte_status cuda_status(cudaError_t e, const char* what);
+// The argument checks of flyte_gemv (FLYTE_OK or FLYTE_ERR_INVALID_ARG with
+// the message set), shared by the entry points that take its arguments.
+flyte_status check_gemv_args(char trans, int64_t m, int64_t n, double alpha, const void* A, flyte_fmt fa,
+                             int64_t lda, const double* x, int64_t incx, const void* y, int64_t incy);
 
 #define FLYTE_TRY_LAUNCH(what)                                   \
   do {                                                           \

@@ -602,7 +602,8 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
   if (warp == kPcWarps) {
     // producer: every stage of every tile of this block, in order
     uint32_t it = 0;
-    for (int64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
+    bool ok = true;
+    for (int64_t tau = blockIdx.x; tau < ntiles && ok; tau += gridDim.x) {
       const int64_t rb0 = (tau / nchunks) * kPcRowsBlock;
       const int64_t cb = (tau % nchunks) * chunk_cols;
       const int64_t ce = min(n, cb + chunk_cols);
@@ -610,9 +611,9 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
       for (int64_t c0 = cb; c0 < cfull; c0 += SC, ++it) {
         const int st = int(it % S);
         const int cols = int(min(int64_t(SC), cfull - c0));
-        bool ok = true;
         if (lane == 0 && it >= S) ok = mbar_wait(&empty[st], ((it / S) - 1) & 1, status);
-        if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) return;
+        ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+        if (!ok) break;
         if (lane == 0) mbar_arrive_expect_tx(&full[st], uint32_t(8 * cols + kPcRowsBlock * cols * K));
         __syncwarp();
         uint8_t* d = smem + st * kStage;
@@ -631,11 +632,22 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
         }
       }
     }
+    // The copies of the last S stages land before this warp leaves: after a
+    // consumer gave up on a wait, nothing else keeps the block alive while
+    // they are in flight (in normal operation these waits return at once or
+    // when the consumers could proceed anyway).
+    if (lane == 0) {
+      for (uint32_t j = it > uint32_t(S) ? it - S : 0; j < it; ++j) mbar_wait(&full[j % S], (j / S) & 1, nullptr);
+    }
     return;
   }
 
-  // consumer warp: rows rb0 + warp * kPcRows + r of each tile
+  // consumer warp: rows rb0 + warp * kPcRows + r of each tile.  After a wait
+  // that gave up (the status word is set), the warp waits for nothing more
+  // and writes NaN for its rows of this and every later tile, so that the
+  // rows it could not compute are visible as such in y.
   uint32_t it = 0;
+  bool failed = false;
   for (int64_t tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
     const int64_t row0 = (tau / nchunks) * kPcRowsBlock + warp * kPcRows;
     const int64_t chunk = tau % nchunks;
@@ -651,10 +663,13 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
 #pragma unroll
       for (int e = 0; e < 4; ++e) dw_zero(acc[r][e]);
     }
-    for (int64_t c0 = cb; c0 < cfull; c0 += SC, ++it) {
+    for (int64_t c0 = cb; c0 < cfull && !failed; c0 += SC, ++it) {
       const int st = int(it % S);
       const bool got = mbar_wait(&full[st], (it / S) & 1, status);
-      if (!__all_sync(0xFFFFFFFFu, got)) return;   // the producer stops at its next bounded wait
+      if (!__all_sync(0xFFFFFFFFu, got)) {   // the producer stops at its next bounded wait
+        failed = true;
+        break;
+      }
       const uint8_t* d = smem + st * kStage;
       const int cols = int(min(int64_t(SC), cfull - c0));
       auto group = [&](int g) {
@@ -684,7 +699,7 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
     const uint8_t* rowp[kPcRows];
 #pragma unroll
     for (int r = 0; r < kPcRows; ++r) rowp[r] = A + min(row0 + r, m - 1) * lda * K;
-    for (int64_t g = (cfull >> 2) + lane; g < ge; g += 32) {
+    for (int64_t g = (cfull >> 2) + lane; g < ge && !failed; g += 32) {
       const float4 xa = __ldg(reinterpret_cast<const float4*>(x1) + g);
       const float4 xb = __ldg(reinterpret_cast<const float4*>(x2) + g);
       const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
@@ -699,7 +714,7 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
       }
     }
     const int64_t j = (ge << 2) + lane;
-    if (j < ce) {
+    if (j < ce && !failed) {
 #pragma unroll
       for (int r = 0; r < kPcRows; ++r) {
         const uint64_t q = load_code_bytes<K>(rowp[r] + j * K);
@@ -708,8 +723,8 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
     }
 #pragma unroll
     for (int r = 0; r < kPcRows; ++r) {
-      double t = row_total(acc[r]);
-      const bool good = __all_sync(0xFFFFFFFFu, ok[r]) && isfinite(t);
+      double t = failed ? __longlong_as_double(0x7FF8000000000000ll) : row_total(acc[r]);
+      const bool good = failed || (__all_sync(0xFFFFFFFFu, ok[r]) && isfinite(t));
       const int64_t row = row0 + r;
       if (row >= m) break;
       if (!good) {

@@ -64,16 +64,17 @@ flyte_status scratch_for_current_device(void** out) {
 extern "C" flyte_status flyte_gemv_static(char trans, int64_t m, int64_t n, double alpha, const void* A,
                                           flyte_fmt fa, int64_t lda, const double* x, int64_t incx,
                                           double beta, double* y, int64_t incy, cudaStream_t stream) {
-  const bool shape_ok = (trans == 'N' || trans == 'n' || trans == 'T' || trans == 't') && m >= 0 && n >= 0;
-  if (!shape_ok || m == 0 || n == 0 || alpha == 0.0) {
-    // argument errors and quick returns need no scratch: flyte_gemv handles them
+  // the checks of flyte_gemv come first, so that a bad argument is reported
+  // as such whatever the size of the call
+  flyte::set_error("%s", "");
+  const flyte_status valid = flyte::check_gemv_args(trans, m, n, alpha, A, fa, lda, x, incx, y, incy);
+  if (valid != FLYTE_OK) return valid;
+  if (m == 0 || n == 0 || alpha == 0.0) {
+    // quick returns need no scratch: flyte_gemv handles them
     return flyte_gemv(trans, m, n, alpha, A, fa, lda, x, incx, beta, y, incy, nullptr, 0, stream);
   }
   const char* op = (trans == 'N' || trans == 'n') ? "gemv_n" : "gemv_t";
   const size_t need = flyte_workspace_bytes(op, m, n, 0, fa);
-  if (need == size_t(-1)) {
-    return flyte_gemv(trans, m, n, alpha, A, fa, lda, x, incx, beta, y, incy, nullptr, 0, stream);
-  }
   if (need > kFlyteStaticScratchBytes) {
     flyte::set_error("gemv_static: this call needs %zu bytes of scratch but the built-in scratch holds %zu; "
                      "use flyte_gemv with a caller workspace", need, kFlyteStaticScratchBytes);

@@ -6,7 +6,7 @@
 // is read here with aligned 32-bit loads of the words that hold the group
 // and funnel shifts, so the double-word arithmetic still applies.  Every
 // word read holds at least one byte of the group, so no read leaves the
-// 4-byte words the group occupies.  Used by blas1.cu and batch.cu.
+// 4-byte words the group occupies.  Used by blas1.cu, gemv.cu and batch.cu.
 #pragma once
 
 #include <cstdint>

@@ -76,7 +76,10 @@ class Batch:
         buf[offset:offset + a.size] = torch.from_numpy(a).cuda()
         return buf[offset:]
 
-    def check(self, skip_axpy=False):
+    def check(self, skip_axpy=False, gemv_sample=None):
+        """gemv_sample: check only that many output entries per gemv job (rows of A for 'N', columns
+        for 'T', seeded, always including the first and last), against the oracle on those rows or
+        columns of A alone."""
         for s, h, d in zip(self.specs, self.host, self.dev):
             op, k, base, n, m = s["op"], s["k"], s["base"], s["n"], s["m"]
             if op == 0:
@@ -96,10 +99,22 @@ class Batch:
                 assert np.array_equal(got, want), s
             elif op >= 3:
                 trans = "N" if op == 3 else "T"
-                ref, absum = oracle.gemv(trans, m, n, 1.5, h["A"], (base, k), n, h["xv"], 1, -0.5, h["y0"], 1)
                 got = d["y"].cpu().numpy()
                 L = n if op == 3 else m
-                bound = 4 * (L + 2) * EPS * (1.5 * absum + 0.5 * np.abs(h["y0"])) + 2 * EPS * np.abs(ref)
+                ly = m if op == 3 else n
+                if gemv_sample is None or gemv_sample >= ly:
+                    idx = np.arange(ly)
+                    ref, absum = oracle.gemv(trans, m, n, 1.5, h["A"], (base, k), n, h["xv"], 1, -0.5, h["y0"], 1)
+                else:
+                    g = np.random.default_rng(ly * 7 + L)
+                    idx = np.unique(np.concatenate([[0, ly - 1], g.integers(0, ly, gemv_sample)]))
+                    codes = h["A"].reshape(m, n, k)
+                    sub = np.ascontiguousarray(codes[idx] if op == 3 else codes[:, idx]).reshape(-1)
+                    mm, nn = (idx.size, n) if op == 3 else (m, idx.size)
+                    ref, absum = oracle.gemv(trans, mm, nn, 1.5, sub, (base, k), nn, h["xv"], 1, -0.5,
+                                             h["y0"][idx], 1)
+                    got = got[idx]
+                bound = 4 * (L + 2) * EPS * (1.5 * absum + 0.5 * np.abs(h["y0"][idx])) + 2 * EPS * np.abs(ref)
                 assert np.all(np.abs(got - ref) <= bound), s
 
 
@@ -154,6 +169,33 @@ def test_batch_misaligned_and_edges():
                                        xv=b.dev[0]["x"])])   # gemv side above the batch limit
 
 
+# The batched workload's own size distribution (vector lengths log-uniform in 10^3..10^6, gemv sides
+# log-uniform in 64..4096), plus jobs that reach the paths only large sides take: 'T' jobs several
+# 1024-column blocks wide and gemv jobs whose x (staged in shared memory) has 4096 entries.
+CONFIG5 = inputs.batch_specs(40, seed=11, len_range=(1e3, 1e6), side_range=(64, 4096)) + [
+    {"op": 4, "k": 5, "base": 1, "n": 4096, "m": 1500},     # 'T', 4 column blocks, x of 1500
+    {"op": 4, "k": 3, "base": 0, "n": 3001, "m": 4096},     # 'T', 3 blocks + ragged, x of 4096
+    {"op": 3, "k": 6, "base": 1, "n": 4096, "m": 700},      # 'N', x of 4096
+    {"op": 3, "k": 2, "base": 1, "n": 4095, "m": 4096},     # 'N', ragged rows, x of 4095
+    {"op": 4, "k": 7, "base": 1, "n": 2049, "m": 4096},     # 'T', 3 blocks, one of a single column
+]
+
+
+def _config5_run():
+    b = Batch(CONFIG5, seed=12)
+    assert any(s["op"] == 4 and s["n"] > 1024 for s in CONFIG5)
+    assert max(s["n"] if s["op"] == 3 else s["m"] for s in CONFIG5 if s["op"] >= 3) == 4096
+    ws = flyte.batch_prepare(b.jobs)
+    flyte.batch_launch(ws)
+    sync()
+    b.check(gemv_sample=200)
+
+
+def test_batch_config5_sizes_default_tiles():
+    """Runs before any autotuning in this file: the built-in tile table."""
+    _config5_run()
+
+
 def test_batch_autotune_then_run():
     flyte.batch_autotune()
     b = Batch(SPECS[:60], seed=4)
@@ -161,3 +203,9 @@ def test_batch_autotune_then_run():
     flyte.batch_launch(ws)
     sync()
     b.check()
+
+
+def test_batch_config5_sizes_autotuned_tiles():
+    """The same jobs after flyte_batch_autotune has filled the tile table."""
+    flyte.batch_autotune()
+    _config5_run()
