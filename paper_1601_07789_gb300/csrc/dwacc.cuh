@@ -168,6 +168,84 @@ __device__ __forceinline__ bool flt_in_window(uint32_t f) {
   return ((f << 1) - (kElo << 24)) < (uint32_t(2 * kWinLog2) << 24);
 }
 
+// ---- pairs of binary32 values (f32x2) ------------------------------------------
+//
+// sm_100-family GPUs add, subtract, multiply and fma two binary32 values held
+// in one 64-bit register with one instruction (add/sub/mul/fma.rn.f32x2),
+// each value rounded exactly as the scalar _rn operation rounds it.  The
+// binary32 rate per value is unchanged (measured on GB300: about 135 value
+// operations per clock and SM for fma.rn.f32 and for fma.rn.f32x2 alike), but
+// a pair costs one issue slot instead of two, which is what the issue-bound
+// gemv kernels need.  The error-free transformations below are the scalar
+// ones of this file applied to both values of a pair.
+
+using f2 = unsigned long long;
+
+__device__ __forceinline__ f2 f2_pack(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ f2 f2_neg(f2 a) { return a ^ 0x8000000080000000ull; }
+
+struct DW2 {
+  f2 hi, lo;   // two double-word accumulators, one per value of the pair
+};
+
+__device__ __forceinline__ void dw2_zero(DW2& a) { a.hi = 0ull; a.lo = 0ull; }
+
+// The two double-word accumulators held by a pair, as scalar DW values.
+__device__ __forceinline__ void dw2_split(const DW2& a, DW& d0, DW& d1) {
+  f2_unpack(a.hi, d0.hi, d1.hi);
+  f2_unpack(a.lo, d0.lo, d1.lo);
+}
+
+// acc <- acc + (p + e), given pn = -p (negation is exact): dw_add_lazy on both values
+// (s + t = S + p by TwoSum written with -pn, then C <- (C + t) + e').
+__device__ __forceinline__ void dw2_add_lazy_neg(DW2& acc, f2 pn, f2 e) {
+  const f2 s = f2_sub(acc.hi, pn);
+  const f2 bp = f2_sub(s, acc.hi);
+  const f2 ap = f2_sub(s, bp);
+  const f2 t = f2_sub(f2_sub(acc.hi, ap), f2_add(pn, bp));
+  acc.lo = f2_add(f2_add(acc.lo, t), e);
+  acc.hi = s;
+}
+
+// The renormalising step (dw_add) on both values, with pn = -p.
+__device__ __forceinline__ void dw2_add_neg(DW2& acc, f2 pn, f2 e) {
+  const f2 s = f2_sub(acc.hi, pn);
+  const f2 bp = f2_sub(s, acc.hi);
+  const f2 ap = f2_sub(s, bp);
+  const f2 t = f2_sub(f2_sub(acc.hi, ap), f2_add(pn, bp));
+  const f2 v = f2_add(f2_add(acc.lo, t), e);
+  const f2 hi = f2_add(s, v);
+  acc.lo = f2_sub(v, f2_sub(hi, s));
+  acc.hi = hi;
+}
+
 // Product of an in-window element (hi + lo) with x = x1 + x2 as (p, e').
 __device__ __forceinline__ void pair_times_x(float ahi, float alo, float x1, float x2, float& p,
                                              float& e) {

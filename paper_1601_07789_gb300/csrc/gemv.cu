@@ -52,6 +52,80 @@ __device__ __forceinline__ void fold(typename Native<BASE>::bits u, float x1, fl
   }
 }
 
+// ---- the fold: element times x1 + x2 into a double-word accumulator -----------------
+//
+// Elements are widened to binary32 (dbl_to_pair) and folded two at a time on
+// the f32x2 pipe (dwacc.cuh): TwoProd of the element with x1, the x2 and low
+// part products into the error word, and the (lazy or renormalising)
+// double-word addition.
+//
+// Window test value of an element: in window iff below window_limit<BASE>().
+// The kernels keep the running unsigned maximum of these values, so a whole
+// row chunk or tile is tested with one compare.
+template <int BASE>
+__host__ __device__ constexpr uint32_t window_limit() {
+  return BASE == FLYTE_F64 ? uint32_t(2 * kWinLog2) << 21 : uint32_t(2 * kWinLog2) << 24;
+}
+
+// Element bits -> binary32 value hi (+ lo for double-based k >= 5, else 0); returns the window value.
+template <int BASE, int K>
+__device__ __forceinline__ uint32_t widen_pair_v(typename Native<BASE>::bits u, float& hi, float& lo) {
+  if constexpr (BASE == FLYTE_F64) {
+    const uint32_t h = uint32_t(u >> 32);
+    (void)dbl_to_pair<K>(h, uint32_t(u), hi, lo);
+    return (h << 1) - ((1023u - kWinLog2) << 21);
+  } else {
+    hi = __uint_as_float(u);
+    lo = 0.f;
+    return (u << 1) - ((127u - kWinLog2) << 24);
+  }
+}
+
+// acc <- acc + (a0, a1) * x for the pair of elements (a0 = h0 + l0, a1 = h1 + l1) and
+// x = X1 + X2 per value (N1 = -X1): pair_times_x and dw_add(_lazy) of dwacc.cuh on both values.
+template <int BASE, int K, bool LAZY>
+__device__ __forceinline__ void fold_pair2(float h0, float l0, float h1, float l1, f2 X1, f2 N1, f2 X2, DW2& acc) {
+  const f2 A = f2_pack(h0, h1);
+  const f2 pn = f2_mul(A, N1);          // -p exactly
+  f2 t = f2_fma(A, X1, pn);             // a x1 - p exactly
+  if constexpr (BASE == FLYTE_F64 && K >= 5) t = f2_fma(f2_pack(l0, l1), X1, t);
+  const f2 e = f2_fma(A, X2, t);
+  if constexpr (LAZY) {
+    dw2_add_lazy_neg(acc, pn, e);
+  } else {
+    dw2_add_neg(acc, pn, e);
+  }
+}
+
+// A 4-element group of one row: elements 0, 1 into acc[0], elements 2, 3 into acc[1].
+template <int BASE, int K, bool LAZY, int NW>
+__device__ __forceinline__ void fold_group2(const uint32_t (&w)[NW], const f2 (&X1)[2], const f2 (&N1)[2],
+                                            const f2 (&X2)[2], DW2 (&acc)[2], uint32_t& vmax) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    float h0, l0, h1, l1;
+    const uint32_t v0 = widen_pair_v<BASE, K>(extract_widened<BASE, K>(w, 2 * q), h0, l0);
+    const uint32_t v1 = widen_pair_v<BASE, K>(extract_widened<BASE, K>(w, 2 * q + 1), h1, l1);
+    vmax = max(vmax, max(v0, v1));
+    fold_pair2<BASE, K, LAZY>(h0, l0, h1, l1, X1[q], N1[q], X2[q], acc[q]);
+  }
+}
+
+// One element (the ragged end of a row): into value 0 of acc; value 1 adds 0 * 0.
+template <int BASE, int K, bool LAZY>
+__device__ __forceinline__ void fold_one2(typename Native<BASE>::bits u, float x1, float x2, DW2& acc,
+                                          uint32_t& vmax) {
+  float h, l;
+  vmax = max(vmax, widen_pair_v<BASE, K>(u, h, l));
+  fold_pair2<BASE, K, LAZY>(h, l, 0.f, 0.f, f2_pack(x1, 0.f), f2_pack(-x1, 0.f), f2_pack(x2, 0.f), acc);
+}
+
+// The four scalar slots (elements 0..3 of the groups) of a row's two pair accumulators.
+__device__ __forceinline__ void dw2_slots(const DW2 (&acc)[2], DW (&d)[4]) {
+  dw2_split(acc[0], d[0], d[1]);
+  dw2_split(acc[1], d[2], d[3]);
+}
+
 // Sum of a row's four slot accumulators over the warp, in double-word
 // arithmetic (depth 2 + 5), as the binary64 value of lane 0 (exact
 // conversion), broadcast to the warp.
@@ -139,9 +213,6 @@ __global__ void __launch_bounds__(256) prep_x(const double* __restrict__ x, int6
 #ifndef FLYTE_PC_CHUNK
 #define FLYTE_PC_CHUNK 4096            // columns per 'N' tile (at most)
 #endif
-#ifndef FLYTE_GEMV_PREFETCH_N
-#define FLYTE_GEMV_PREFETCH_N 0
-#endif
 #ifndef FLYTE_GEMV_PREFETCH_T
 #define FLYTE_GEMV_PREFETCH_T 0
 #endif
@@ -186,68 +257,46 @@ __global__ void __launch_bounds__(kNWarps * 32) gemv_n_kernel(
 #pragma unroll
   for (int r = 0; r < kNRowsPerWarp; ++r) { v[r] = 0.0; ok[r] = fast != 0; }
   if (fast) {
-    DW acc[kNRowsPerWarp][4];
+    DW2 acc[kNRowsPerWarp][2];
+    uint32_t vmax[kNRowsPerWarp];
 #pragma unroll
-    for (int r = 0; r < kNRowsPerWarp; ++r)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) dw_zero(acc[r][e]);
+    for (int r = 0; r < kNRowsPerWarp; ++r) {
+      vmax[r] = 0u;
+      dw2_zero(acc[r][0]);
+      dw2_zero(acc[r][1]);
+    }
     int64_t g = gb + lane;
-    auto load_batch = [&](int64_t g0, float4 (&xa)[kNUnroll], float4 (&xb)[kNUnroll],
+    auto load_batch = [&](int64_t g0, ulonglong2 (&xa)[kNUnroll], ulonglong2 (&xb)[kNUnroll],
                           uint32_t (&w)[kNUnroll][kNRowsPerWarp][K]) {
 #pragma unroll
       for (int u = 0; u < kNUnroll; ++u) {
         const int64_t gu = g0 + 32 * u;
-        xa[u] = __ldg(reinterpret_cast<const float4*>(x1) + gu);
-        xb[u] = __ldg(reinterpret_cast<const float4*>(x2) + gu);
+        xa[u] = __ldg(reinterpret_cast<const ulonglong2*>(x1) + gu);
+        xb[u] = __ldg(reinterpret_cast<const ulonglong2*>(x2) + gu);
 #pragma unroll
         for (int r = 0; r < kNRowsPerWarp; ++r) load_grp<K, UA>(rowp[r] + gu * (4 * K), w[u][r]);
       }
     };
-#if FLYTE_GEMV_PREFETCH_N
-    float4 nxa[kNUnroll], nxb[kNUnroll];
-    uint32_t nw[kNUnroll][kNRowsPerWarp][K];
-    if (g + 32 * (kNUnroll - 1) < ge) load_batch(g, nxa, nxb, nw);
-#endif
     for (; g + 32 * (kNUnroll - 1) < ge; g += 32 * kNUnroll) {
-      float4 xa[kNUnroll], xb[kNUnroll];
+      ulonglong2 xa[kNUnroll], xb[kNUnroll];
       uint32_t w[kNUnroll][kNRowsPerWarp][K];
-#if FLYTE_GEMV_PREFETCH_N
-#pragma unroll
-      for (int u = 0; u < kNUnroll; ++u) {
-        xa[u] = nxa[u];
-        xb[u] = nxb[u];
-#pragma unroll
-        for (int r = 0; r < kNRowsPerWarp; ++r)
-#pragma unroll
-          for (int j = 0; j < K; ++j) w[u][r][j] = nw[u][r][j];
-      }
-      if (g + 32 * kNUnroll + 32 * (kNUnroll - 1) < ge) load_batch(g + 32 * kNUnroll, nxa, nxb, nw);
-#else
       load_batch(g, xa, xb, w);
-#endif
 #pragma unroll
       for (int u = 0; u < kNUnroll; ++u) {
-        const float xs1[4] = {xa[u].x, xa[u].y, xa[u].z, xa[u].w};
-        const float xs2[4] = {xb[u].x, xb[u].y, xb[u].z, xb[u].w};
+        const f2 X1[2] = {xa[u].x, xa[u].y}, N1[2] = {f2_neg(xa[u].x), f2_neg(xa[u].y)}, X2[2] = {xb[u].x, xb[u].y};
 #pragma unroll
-        for (int r = 0; r < kNRowsPerWarp; ++r)
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            fold<BASE, K, LAZY>(extract_widened<BASE, K>(w[u][r], e), xs1[e], xs2[e], acc[r][e], ok[r]);
+        for (int r = 0; r < kNRowsPerWarp; ++r) fold_group2<BASE, K, LAZY>(w[u][r], X1, N1, X2, acc[r], vmax[r]);
       }
     }
     for (; g < ge; g += 32) {
-      const float4 xa = __ldg(reinterpret_cast<const float4*>(x1) + g);
-      const float4 xb = __ldg(reinterpret_cast<const float4*>(x2) + g);
-      const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
-      const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
+      const ulonglong2 xa = __ldg(reinterpret_cast<const ulonglong2*>(x1) + g);
+      const ulonglong2 xb = __ldg(reinterpret_cast<const ulonglong2*>(x2) + g);
+      const f2 X1[2] = {xa.x, xa.y}, N1[2] = {f2_neg(xa.x), f2_neg(xa.y)}, X2[2] = {xb.x, xb.y};
 #pragma unroll
       for (int r = 0; r < kNRowsPerWarp; ++r) {
         uint32_t w[K];
         load_grp<K, UA>(rowp[r] + g * (4 * K), w);
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
+        fold_group2<BASE, K, LAZY>(w, X1, N1, X2, acc[r], vmax[r]);
       }
     }
     const int64_t j = (ge << 2) + lane;               // trailing n % 4 elements (last chunk only)
@@ -255,14 +304,16 @@ __global__ void __launch_bounds__(kNWarps * 32) gemv_n_kernel(
 #pragma unroll
       for (int r = 0; r < kNRowsPerWarp; ++r) {
         const uint64_t q = load_code_bytes<K>(rowp[r] + j * K);
-        fold<BASE, K, LAZY>(widen<BASE, K>(q), x1[j], x2[j], acc[r][0], ok[r]);
+        fold_one2<BASE, K, LAZY>(widen<BASE, K>(q), x1[j], x2[j], acc[r][0], vmax[r]);
       }
     }
 #pragma unroll
     for (int r = 0; r < kNRowsPerWarp; ++r) {
-      const double t = row_total(acc[r]);
+      DW slots[4];
+      dw2_slots(acc[r], slots);
+      const double t = row_total(slots);
       v[r] = t;
-      ok[r] = __all_sync(0xFFFFFFFFu, ok[r]) && isfinite(t);
+      ok[r] = __all_sync(0xFFFFFFFFu, vmax[r] < window_limit<BASE>()) && isfinite(t);
     }
   }
 #pragma unroll
@@ -349,6 +400,25 @@ __device__ __forceinline__ void fold_parities(DW (&acc)[2][4], DW (&tot)[4]) {
   }
 }
 
+// The same for pair accumulators: acc[parity][q] holds columns 2q and 2q + 1.
+__device__ __forceinline__ void fold_parities2(DW2 (&acc)[2][2], DW (&tot)[4]) {
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    DW a[2], b[2];
+    dw2_split(acc[0][q], a[0], a[1]);
+    dw2_split(acc[1][q], b[0], b[1]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      dw_norm(a[h]);
+      dw_norm(b[h]);
+      dw_add_dw(a[h], b[h]);
+      dw_add_dw(tot[2 * q + h], a[h]);
+    }
+    dw2_zero(acc[0][q]);
+    dw2_zero(acc[1][q]);
+  }
+}
+
 template <int BASE, int K, bool LAZY, bool UA>
 __global__ void __launch_bounds__(kTThreads, t_min_blocks<K>()) gemv_t_kernel(
     const uint8_t* __restrict__ A, int64_t lda, int64_t m, int64_t n, const float* __restrict__ x1,
@@ -362,72 +432,153 @@ __global__ void __launch_bounds__(kTThreads, t_min_blocks<K>()) gemv_t_kernel(
   const int64_t i1 = min(m, i0 + rb);
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   bool ok = fast && c0 + 4 <= n;
-  if (ok) {
-    const uint8_t* colp = A + c0 * K;
-    DW acc[2][4], tot[4];
+  // Pairs of columns on the f32x2 pipe for double-based k = 4 (0.220 -> 0.208 ms at 16384^2); the
+  // scalar fold elsewhere, where the pair fold measured slower (k = 3: 0.232 -> 0.244 ms, k = 5:
+  // 0.303 -> 0.368 ms, same GPU and build)
+  constexpr bool kPairs = BASE == FLYTE_F64 && K == 4;
+  if constexpr (kPairs) {
+    if (ok) {
+      const uint8_t* colp = A + c0 * K;
+      DW2 acc[2][2];
+      DW tot[4];
+      uint32_t vmax = 0u;
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      dw_zero(acc[0][e]);
-      dw_zero(acc[1][e]);
-      dw_zero(tot[e]);
-    }
-    int64_t since = 0;
-    int64_t i = i0;
-    auto load_batch = [&](int64_t r, uint32_t (&w)[U][K], float (&b1)[U], float (&b2)[U]) {
-#pragma unroll
-      for (int u = 0; u < U; u += 4) {
-        const float4 p = __ldg(reinterpret_cast<const float4*>(x1 + r + u));
-        const float4 q = __ldg(reinterpret_cast<const float4*>(x2 + r + u));
-        b1[u] = p.x; b1[u + 1] = p.y; b1[u + 2] = p.z; b1[u + 3] = p.w;
-        b2[u] = q.x; b2[u + 1] = q.y; b2[u + 2] = q.z; b2[u + 3] = q.w;
+      for (int q = 0; q < 2; ++q) {
+        dw2_zero(acc[0][q]);
+        dw2_zero(acc[1][q]);
       }
 #pragma unroll
-      for (int u = 0; u < U; ++u) load_grp<K, UA>(colp + (r + u) * lda * K, w[u]);
-    };
+      for (int e = 0; e < 4; ++e) dw_zero(tot[e]);
+      int64_t since = 0;
+      int64_t i = i0;
+      auto load_batch = [&](int64_t r, uint32_t (&w)[U][K], float (&b1)[U], float (&b2)[U]) {
+#pragma unroll
+        for (int u = 0; u < U; u += 4) {
+          const float4 p = __ldg(reinterpret_cast<const float4*>(x1 + r + u));
+          const float4 q = __ldg(reinterpret_cast<const float4*>(x2 + r + u));
+          b1[u] = p.x; b1[u + 1] = p.y; b1[u + 2] = p.z; b1[u + 3] = p.w;
+          b2[u] = q.x; b2[u + 1] = q.y; b2[u + 2] = q.z; b2[u + 3] = q.w;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_grp<K, UA>(colp + (r + u) * lda * K, w[u]);
+      };
 #if FLYTE_GEMV_PREFETCH_T
-    // software pipeline: the next batch of rows is in flight while this one is folded
-    uint32_t wn[U][K];
-    float n1[U], n2[U];
-    if (i + U <= i1) load_batch(i, wn, n1, n2);
+      // software pipeline: the next batch of rows is in flight while this one is folded
+      uint32_t wn[U][K];
+      float n1[U], n2[U];
+      if (i + U <= i1) load_batch(i, wn, n1, n2);
 #endif
-    for (; i + U <= i1; i += U) {
-      uint32_t w[U][K];
-      float a1[U], a2[U];
+      for (; i + U <= i1; i += U) {
+        uint32_t w[U][K];
+        float a1[U], a2[U];
 #if FLYTE_GEMV_PREFETCH_T
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        a1[u] = n1[u];
-        a2[u] = n2[u];
+        for (int u = 0; u < U; ++u) {
+          a1[u] = n1[u];
+          a2[u] = n2[u];
 #pragma unroll
-        for (int j = 0; j < K; ++j) w[u][j] = wn[u][j];
-      }
-      if (i + 2 * U <= i1) load_batch(i + U, wn, n1, n2);
+          for (int j = 0; j < K; ++j) w[u][j] = wn[u][j];
+        }
+        if (i + 2 * U <= i1) load_batch(i + U, wn, n1, n2);
 #else
-      load_batch(i, w, a1, a2);
+        load_batch(i, w, a1, a2);
 #endif
 #pragma unroll
-      for (int u = 0; u < U; ++u)
+        for (int u = 0; u < U; ++u) {
+          // the row's x for all four columns of the thread
+          const f2 X1 = f2_pack(a1[u], a1[u]), X2 = f2_pack(a2[u], a2[u]);
+          const f2 X1s[2] = {X1, X1}, N1s[2] = {f2_neg(X1), f2_neg(X1)}, X2s[2] = {X2, X2};
+          fold_group2<BASE, K, LAZY>(w[u], X1s, N1s, X2s, acc[u & 1], vmax);
+        }
+        since += U;
+        if (since >= fold_rows) {
+          fold_parities2(acc, tot);
+          since = 0;
+        }
+      }
+      for (; i < i1; ++i) {
+        uint32_t w[K];
+        load_grp<K, UA>(colp + i * lda * K, w);
+        const f2 X1 = f2_pack(x1[i], x1[i]), X2 = f2_pack(x2[i], x2[i]);
+        const f2 X1s[2] = {X1, X1}, N1s[2] = {f2_neg(X1), f2_neg(X1)}, X2s[2] = {X2, X2};
+        fold_group2<BASE, K, LAZY>(w, X1s, N1s, X2s, acc[0], vmax);
+      }
+      fold_parities2(acc, tot);
+      ok = vmax < window_limit<BASE>();
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          fold<BASE, K, LAZY>(extract_widened<BASE, K>(w[u], e), a1[u], a2[u], acc[u & 1][e], ok);
-      since += U;
-      if (since >= fold_rows) {
-        fold_parities(acc, tot);
-        since = 0;
+      for (int e = 0; e < 4; ++e) {
+        v[e] = dw_value(tot[e]);      // exact: tot is normalised
+        ok = ok && isfinite(v[e]);
       }
     }
-    for (; i < i1; ++i) {
-      uint32_t w[K];
-      load_grp<K, UA>(colp + i * lda * K, w);
-      const float a1 = x1[i], a2 = x2[i];
+  } else {
+    if (ok) {
+      const uint8_t* colp = A + c0 * K;
+      DW acc[2][4], tot[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), a1, a2, acc[0][e], ok);
-    }
-    fold_parities(acc, tot);
+      for (int e = 0; e < 4; ++e) {
+        dw_zero(acc[0][e]);
+        dw_zero(acc[1][e]);
+        dw_zero(tot[e]);
+      }
+      int64_t since = 0;
+      int64_t i = i0;
+      auto load_batch = [&](int64_t r, uint32_t (&w)[U][K], float (&b1)[U], float (&b2)[U]) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      v[e] = dw_value(tot[e]);      // exact: tot is normalised
-      ok = ok && isfinite(v[e]);
+        for (int u = 0; u < U; u += 4) {
+          const float4 p = __ldg(reinterpret_cast<const float4*>(x1 + r + u));
+          const float4 q = __ldg(reinterpret_cast<const float4*>(x2 + r + u));
+          b1[u] = p.x; b1[u + 1] = p.y; b1[u + 2] = p.z; b1[u + 3] = p.w;
+          b2[u] = q.x; b2[u + 1] = q.y; b2[u + 2] = q.z; b2[u + 3] = q.w;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) load_grp<K, UA>(colp + (r + u) * lda * K, w[u]);
+      };
+#if FLYTE_GEMV_PREFETCH_T
+      // software pipeline: the next batch of rows is in flight while this one is folded
+      uint32_t wn[U][K];
+      float n1[U], n2[U];
+      if (i + U <= i1) load_batch(i, wn, n1, n2);
+#endif
+      for (; i + U <= i1; i += U) {
+        uint32_t w[U][K];
+        float a1[U], a2[U];
+#if FLYTE_GEMV_PREFETCH_T
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          a1[u] = n1[u];
+          a2[u] = n2[u];
+#pragma unroll
+          for (int j = 0; j < K; ++j) w[u][j] = wn[u][j];
+        }
+        if (i + 2 * U <= i1) load_batch(i + U, wn, n1, n2);
+#else
+        load_batch(i, w, a1, a2);
+#endif
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            fold<BASE, K, LAZY>(extract_widened<BASE, K>(w[u], e), a1[u], a2[u], acc[u & 1][e], ok);
+        since += U;
+        if (since >= fold_rows) {
+          fold_parities(acc, tot);
+          since = 0;
+        }
+      }
+      for (; i < i1; ++i) {
+        uint32_t w[K];
+        load_grp<K, UA>(colp + i * lda * K, w);
+        const float a1 = x1[i], a2 = x2[i];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), a1, a2, acc[0][e], ok);
+      }
+      fold_parities(acc, tot);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        v[e] = dw_value(tot[e]);      // exact: tot is normalised
+        ok = ok && isfinite(v[e]);
+      }
     }
   }
   if (!ok) {
@@ -655,13 +806,13 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
     const int64_t ce = min(n, cb + chunk_cols);
     const int64_t ge = ce >> 2;
     const int64_t cfull = cb + ((ce - cb) >> 7 << 7);
-    DW acc[kPcRows][4];
-    bool ok[kPcRows];
+    DW2 acc[kPcRows][2];
+    uint32_t vmax[kPcRows];
 #pragma unroll
     for (int r = 0; r < kPcRows; ++r) {
-      ok[r] = true;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) dw_zero(acc[r][e]);
+      vmax[r] = 0u;
+      dw2_zero(acc[r][0]);
+      dw2_zero(acc[r][1]);
     }
     for (int64_t c0 = cb; c0 < cfull && !failed; c0 += SC, ++it) {
       const int st = int(it % S);
@@ -673,17 +824,14 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
       const uint8_t* d = smem + st * kStage;
       const int cols = int(min(int64_t(SC), cfull - c0));
       auto group = [&](int g) {
-        const float4 xa = reinterpret_cast<const float4*>(d)[g];
-        const float4 xb = reinterpret_cast<const float4*>(d + 4 * SC)[g];
-        const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
-        const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
+        const ulonglong2 xa = reinterpret_cast<const ulonglong2*>(d)[g];
+        const ulonglong2 xb = reinterpret_cast<const ulonglong2*>(d + 4 * SC)[g];
+        const f2 X1[2] = {xa.x, xa.y}, N1[2] = {f2_neg(xa.x), f2_neg(xa.y)}, X2[2] = {xb.x, xb.y};
 #pragma unroll
         for (int r = 0; r < kPcRows; ++r) {
           uint32_t w[K];
           lds_group<K>(d + 8 * SC + (warp * kPcRows + r) * kRowBytes + g * 4 * K, w);
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
+          fold_group2<BASE, K, LAZY>(w, X1, N1, X2, acc[r], vmax[r]);
         }
       };
       if (FLYTE_PC_UNROLL_FULL && cols == SC) {
@@ -700,17 +848,14 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
 #pragma unroll
     for (int r = 0; r < kPcRows; ++r) rowp[r] = A + min(row0 + r, m - 1) * lda * K;
     for (int64_t g = (cfull >> 2) + lane; g < ge && !failed; g += 32) {
-      const float4 xa = __ldg(reinterpret_cast<const float4*>(x1) + g);
-      const float4 xb = __ldg(reinterpret_cast<const float4*>(x2) + g);
-      const float xs1[4] = {xa.x, xa.y, xa.z, xa.w};
-      const float xs2[4] = {xb.x, xb.y, xb.z, xb.w};
+      const ulonglong2 xa = __ldg(reinterpret_cast<const ulonglong2*>(x1) + g);
+      const ulonglong2 xb = __ldg(reinterpret_cast<const ulonglong2*>(x2) + g);
+      const f2 X1[2] = {xa.x, xa.y}, N1[2] = {f2_neg(xa.x), f2_neg(xa.y)}, X2[2] = {xb.x, xb.y};
 #pragma unroll
       for (int r = 0; r < kPcRows; ++r) {
         uint32_t w[K];
         load_group<K>(rowp[r] + g * (4 * K), w);
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          fold<BASE, K, LAZY>(extract_widened<BASE, K>(w, e), xs1[e], xs2[e], acc[r][e], ok[r]);
+        fold_group2<BASE, K, LAZY>(w, X1, N1, X2, acc[r], vmax[r]);
       }
     }
     const int64_t j = (ge << 2) + lane;
@@ -718,13 +863,15 @@ __global__ void __launch_bounds__(pc_threads<K>()) gemv_n_pc(
 #pragma unroll
       for (int r = 0; r < kPcRows; ++r) {
         const uint64_t q = load_code_bytes<K>(rowp[r] + j * K);
-        fold<BASE, K, LAZY>(widen<BASE, K>(q), x1[j], x2[j], acc[r][0], ok[r]);
+        fold_one2<BASE, K, LAZY>(widen<BASE, K>(q), x1[j], x2[j], acc[r][0], vmax[r]);
       }
     }
 #pragma unroll
     for (int r = 0; r < kPcRows; ++r) {
-      double t = failed ? __longlong_as_double(0x7FF8000000000000ll) : row_total(acc[r]);
-      const bool good = failed || (__all_sync(0xFFFFFFFFu, ok[r]) && isfinite(t));
+      DW slots[4];
+      dw2_slots(acc[r], slots);
+      double t = failed ? __longlong_as_double(0x7FF8000000000000ll) : row_total(slots);
+      const bool good = failed || (__all_sync(0xFFFFFFFFu, vmax[r] < window_limit<BASE>()) && isfinite(t));
       const int64_t row = row0 + r;
       if (row >= m) break;
       if (!good) {

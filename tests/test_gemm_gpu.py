@@ -1,8 +1,8 @@
 """GPU parity of flyte_gemm against the CPU oracle (Dot2 entries).
 
 Bounds (header tolerances):
-  float-based:  |C - C_ref| <= 2^-22 (|alpha| sum_l |A_il B_lj| + |beta C0_ij|) for mixed-sign data,
-                2^-20 (same sums) for any data (the tensor core truncates; see test_gemm_positive_long_k)
+  float-based:  |C - C_ref| <= 2^-22 (|alpha| sum_l |A_il B_lj| + |beta C0_ij|), mixed-sign and
+                same-sign data alike (test_gemm_same_sign_long_k)
   double-based: |C - C_ref| <= 4 k 2^-53 (|alpha| sum_l |A_il B_lj| + |beta C0_ij|) + 2^-52 |C_ref|
 """
 from __future__ import annotations
@@ -177,20 +177,77 @@ def test_gemm_packed_c(f, kc):
 
 
 @pytest.mark.parametrize("k", [2, 3, 4])
-def test_gemm_positive_long_k(k):
-    """All-positive operands (no cancellation: partial sums grow to sum|ab|) with a long K.  The tensor
-    core's binary32 accumulation truncates, so same-sign data carry a one-signed error of up to about
-    2^-21 sum|ab| (measured 2.26-2.65 x 2^-22 at K = 8192, whatever the chunking): the float-based gemm
-    is held to 2^-20 sum|ab| for any data and to 2^-22 for mixed signs (the tests above)."""
-    M, N, K = 384, 640, 8192
+@pytest.mark.parametrize("dist,K", [("u01", 8192), ("absn", 2048), ("neg", 8192)])
+def test_gemm_same_sign_long_k(k, dist, K):
+    """Operands of one sign (no cancellation: the partial sums grow to sum|ab| and the tensor core's
+    truncation errors all point one way) with a long K, held to the same 2^-22 sum|ab| as mixed signs."""
+    M, N = 384, 640
     f = (k, 0)
-    A = _codes(np.random.default_rng(21).uniform(0, 1, M * K).astype(np.float32), f)
-    B = _codes(np.random.default_rng(22).uniform(0, 1, K * N).astype(np.float32), f)
+    g1, g2 = np.random.default_rng(21), np.random.default_rng(22)
+    if dist == "absn":
+        a, b = np.abs(g1.standard_normal(M * K)), np.abs(g2.standard_normal(K * N))
+    else:
+        a, b = g1.uniform(0, 1, M * K), g2.uniform(0, 1, K * N)
+        if dist == "neg":
+            a = -a
+    A = _codes(a.astype(np.float32), f)
+    B = _codes(b.astype(np.float32), f)
     got = run_gemm(M, N, K, f, A, K, B, N)
     s = np.random.default_rng(23)
-    rows = s.integers(0, M, 1024)
-    cols = s.integers(0, N, 1024)
-    ref, absum = oracle.gemm_entries(rows, cols, K, 1.0, A, (0, k), K, B, (0, k), N)
-    err = np.abs(got[rows, cols].astype(np.float64) - ref)
-    assert np.all(err <= 2.0 ** -20 * absum), f"worst {np.max(err / (2.0 ** -20 * absum)):.3g} of 2^-20 sum|ab|"
-    print(f"k={k}: worst error = {np.max(err / (2.0 ** -22 * absum)):.3g} x 2^-22 sum|ab|")
+    rows = s.integers(0, M, 2048)
+    cols = s.integers(0, N, 2048)
+    worst = check(got, M, N, K, f, A, K, B, N, 1.0, 0.0, None, rows, cols)
+    print(f"k={k} {dist} K={K}: worst error = {worst:.3g} x 2^-22 sum|ab|")
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_gemm_near_float_max(k):
+    """Entries up to the largest binary32 values times small partners: finite products, so the
+    split into bf16 parts must stay finite (no rounding of the top part up to infinity)."""
+    m, n, kk = 130, 140, 96
+    f = (k, 0)
+    g = np.random.default_rng(31)
+    a = g.uniform(-1, 1, m * kk).astype(np.float32)
+    a[::7] = np.float32(3.4e38) * np.sign(g.uniform(-1, 1, a[::7].size)).astype(np.float32)
+    a[3::11] = np.float32(-3.3962e38)                       # just above the bf16 rounding threshold 0x7F7F8000
+    b = (g.uniform(-1, 1, kk * n) * 1e-30).astype(np.float32)
+    A, B = _codes(a, f), _codes(b, f)
+    got = run_gemm(m, n, kk, f, A, kk, B, n)
+    assert np.all(np.isfinite(got[:, :n]))
+    check(got, m, n, kk, f, A, kk, B, n, 1.0, 0.0, None)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_gemm_special_values_ieee_class(k):
+    """Inf and NaN inputs (Sec. 5.3): an entry whose sum meets one is NaN when a term is NaN (a NaN
+    input or Inf * 0) or infinities of both signs meet, else the signed infinity; the oracle gives the
+    plain IEEE sum there.  All other entries keep the 2^-22 bound; alpha and beta apply as elsewhere."""
+    m, n, kk = 150, 170, 200
+    f = (k, 0)
+    g = np.random.default_rng(41 + k)
+    a = g.uniform(-1, 1, (m, kk)).astype(np.float32)
+    b = g.uniform(-1, 1, (kk, n)).astype(np.float32)
+    a[3, 10] = np.inf                       # row 3: +Inf times column entries (some made 0 below)
+    a[7, 20] = -np.inf
+    a[7, 21] = np.inf                       # row 7: both signs -> NaN
+    a[11, 30] = np.nan                      # row 11: NaN
+    b[10, 5] = 0.0                          # (3, 5): Inf * 0 -> NaN
+    b[40, 100] = -np.inf                    # column 100: -Inf
+    b[50, 140] = np.nan                     # column 140: NaN
+    A, B = _codes(a.reshape(-1), f), _codes(b.reshape(-1), f)
+    C0 = g.uniform(-1, 1, (m, n))
+    got = run_gemm(m, n, kk, f, A, kk, B, n, alpha=-1.5, beta=0.5, C0=C0)
+    rr, cc = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    rows, cols = rr.reshape(-1), cc.reshape(-1)
+    ref, absum = oracle.gemm_entries(rows, cols, kk, -1.5, A, (0, k), kk, B, (0, k), n, 0.5,
+                                     C0[rows, cols].astype(np.float64))
+    g_ = got[rows, cols].astype(np.float64)
+    special = ~np.isfinite(ref)
+    assert special.sum() > 300
+    assert np.array_equal(np.isnan(g_[special]), np.isnan(ref[special]))
+    inf = special & ~np.isnan(ref)
+    assert np.array_equal(g_[inf], ref[inf])
+    assert np.isnan(g_[special & np.isnan(ref)]).all()
+    fin = ~special
+    bound = 2.0 ** -22 * (1.5 * absum[fin] + 0.5 * np.abs(C0[rows, cols][fin]))
+    assert np.all(np.abs(g_[fin] - ref[fin]) <= bound)
