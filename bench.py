@@ -95,7 +95,8 @@ def run_case(args):
         for _ in range(2):
             flyte.dot(xs, (k, 1), ys, (k, 1))
             flyte.axpy(1.5, xs, (k, 1), ys, (k, 1))      # binary32 alpha: the exact binary32 path
-            flyte.axpy(0.1, xs, (k, 1), ys, (k, 1))      # any other alpha: two binary32 parts
+            flyte.axpy(0.1, xs, (k, 1), ys, (k, 1))      # any other alpha: two binary32 parts (k <= 4)
+            flyte.scal(1.5, xs, (k, 1))                  # in place, the paper's "scale"
     elif args.case == "batch":
         from paper_1601_07789_gb300 import inputs
         specs = inputs.batch_specs(512, seed=5)
@@ -609,7 +610,13 @@ def run_rows(dev, hbm_peak):
     # alpha = 0.1 is not a binary32 number: the two-part binary32 path
     rows["axpy_f64_k4_alpha_not_binary32"] = entry(3 * 4 * n, timeit(lambda: flyte.axpy(0.1, xs, (4, 1), ys, (4, 1), n=n)), 2 * n)
     rows["n"] = n
-    del v, out, xs, ys
+    del xs, ys
+    # double-based k = 5 axpy (x, y as exact binary32 pairs; the binary64 fma was 46 % of HBM)
+    xs5 = flyte.pack(v, 5)
+    gen.manual_seed(1602)
+    ys5 = flyte.pack(torch.randn(n, dtype=torch.float64, device=dev, generator=gen), 5)
+    rows["axpy_f64_k5"] = entry(3 * 5 * n, timeit(lambda: flyte.axpy(1.5, xs5, (5, 1), ys5, (5, 1), n=n)), 2 * n)
+    del v, out, xs5, ys5
     rows.update(run_gemm_rows(dev))
     rows.update(run_refine_rows(dev))
     rows.update(run_batch_rows(dev))
@@ -629,11 +636,22 @@ def run_gemm_rows(dev):
     except Exception:
         pass
     bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
-    fp64_peak = 1.25   # nominal dense FP64 tensor rate of this GPU (TFLOP/s); no measured figure
     out = {}
 
     def timeit(fn, reps):
         return median_ms(fn, stream, reps=reps)
+
+    # binary64 tensor rate measured here and now: cuBLAS DGEMM (torch.matmul, float64) at 4096^3,
+    # the denominator of the double-based rows (as cuBLAS bf16 is the driver's bf16 peak)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    a64 = torch.rand(4096, 4096, dtype=torch.float64, device=dev, generator=gen)
+    b64 = torch.rand(4096, 4096, dtype=torch.float64, device=dev, generator=gen)
+    c64 = torch.empty(4096, 4096, dtype=torch.float64, device=dev)
+    ms64 = timeit(lambda: torch.matmul(a64, b64, out=c64), 10)
+    fp64_peak = 2.0 * 4096 ** 3 / (ms64 * 1e-3) / 1e12
+    out["fp64_peak_cublas_dgemm_4096"] = {"ms": round(ms64, 3), "TFLOPs": round(fp64_peak, 3)}
+    del a64, b64, c64
 
     for k, size, reps in ((2, 8192, 20), (3, 8192, 20), (4, 8192, 20), (5, 4096, 20)):
         base = 0 if k <= 4 else 1
@@ -656,7 +674,7 @@ def run_gemm_rows(dev):
                                             "frac_bf16_peak": round(executed / bf16_peak, 4)}
         else:
             out[f"gemm_f64_k{k}_{size}"] = {"ms": round(ms, 3), "useful_TFLOPs": round(useful, 3),
-                                            "frac_fp64_nominal": round(useful / fp64_peak, 4)}
+                                            "frac_fp64_measured_dgemm": round(useful / fp64_peak, 4)}
         del A, B, C, ws
     return out
 

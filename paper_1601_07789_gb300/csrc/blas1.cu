@@ -27,6 +27,9 @@ namespace flyte {
 namespace {
 
 constexpr int kThreads = 256;
+#ifndef FLYTE_AXPY_WIDE_DIV
+#define FLYTE_AXPY_WIDE_DIV 3          // k = 5..7 axpy: one warp in this many runs the binary64 fma
+#endif
 constexpr int kDotMaxBlocks = 2048;   // fixed, so the workspace size does not depend on the device
 constexpr int kHdrBytes = 256;
 
@@ -184,6 +187,11 @@ __global__ void __launch_bounds__(kThreads) axpy_groups_f32exact(const uint8_t* 
   const float a2 = float(alpha - double(af));
   const float a3 = float(alpha - double(af) - double(a2));
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  // k = 5..7: one warp in FLYTE_AXPY_WIDE_DIV takes the binary64 fma for all its groups, the others
+  // the binary32 decision, so that the fp64 pipe and the binary32/integer pipes work side by side:
+  // either path alone is bound by its own pipe at about the same rate (k = 5 at 2^28 elements:
+  // binary64 1.06 ms, binary32 decision 1.01 ms; one warp in 2, 3, 4 on binary64: 0.87, 0.85, 0.93 ms)
+  const bool wide64 = K >= 5 && ((threadIdx.x >> 5) % FLYTE_AXPY_WIDE_DIV) == 0;
   for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngrp; g += stride) {
     uint32_t wx[K], wy[K], wo[K];
     load_group<K>(X + g * (4 * K), wx);
@@ -191,11 +199,13 @@ __global__ void __launch_bounds__(kThreads) axpy_groups_f32exact(const uint8_t* 
 #pragma unroll
     for (int j = 0; j < K; ++j) wo[j] = 0;
     uint64_t c[4];
-    bool ok = true;
+    bool ok = !wide64;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 4 && !wide64; ++q) {
       const uint64_t ux = extract_widened<FLYTE_F64, K>(wx, q), uy = extract_widened<FLYTE_F64, K>(wy, q);
-      if constexpr (SPLIT) {
+      if constexpr (K >= 5) {
+        ok &= axpy_exact_wide<K, MODE>(ux, uy, af, c[q]);
+      } else if constexpr (SPLIT) {
         ok &= axpy_exact_f32x2<K, MODE>(ux, uy, af, a2, a3, c[q]);
       } else {
         ok &= axpy_exact_f32<K, MODE>(ux, uy, af, c[q]);
@@ -352,15 +362,17 @@ flyte_status launch_axpy(int64_t n, double alpha, const void* x, flyte_fmt fx, i
     if (fx.k == KY && incx == 1 && incy == 1 && aligned(x, S) && aligned(y, S) && n >= 4) {
       const int64_t ngrp = n / 4;
       bool done = false;
-      if constexpr (BASE == FLYTE_F64 && KY >= 2 && KY <= 4) {
-        // alpha inside the window: the exact binary32 paths (one part when alpha is a binary32 number)
+      if constexpr (BASE == FLYTE_F64 && KY >= 2 && KY <= 7) {
+        // alpha inside the window: the exact binary32 paths (one part when alpha is a binary32
+        // number; k = 5..7 take a binary32 alpha only)
         if (std::fabs(alpha) >= 0x1p-40 && std::fabs(alpha) < 0x1p40) {
           if (double(float(alpha)) == alpha) {
             launch_axpy_f32exact<KY, false>(X, Y, ngrp, alpha, mode, s);
-          } else {
+            done = true;
+          } else if constexpr (KY <= 4) {
             launch_axpy_f32exact<KY, true>(X, Y, ngrp, alpha, mode, s);
+            done = true;
           }
-          done = true;
         }
       }
       if (!done) axpy_groups<BASE, KY><<<grid_for(ngrp, kThreads), kThreads, 0, s>>>(X, Y, ngrp, alpha, mode);

@@ -248,12 +248,13 @@ def test_scal_config_mixture_and_paths():
         flyte.scal(1.0, torch.zeros(16, dtype=torch.uint8, device="cuda"), (9, 1), n=2)
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("mode", MODES)
 def test_axpy_binary32_alpha_exact_path(k, mode):
     """alpha exactly representable in binary32 takes the binary32 error-free path for double-based
-    k <= 4: bit-exact against the oracle on data that make exact results, ties, cancellations and
-    out-of-window values (which fall back to binary64) frequent."""
+    k <= 7 (k = 5..7 through the exact hi/lo pairs of x and y): bit-exact against the oracle on data
+    that make exact results, ties, cancellations, near-cancellations and out-of-window values (which
+    fall back to binary64) frequent."""
     f = (k, 1)
     g = np.random.default_rng(40 + k)
     n = 1 << 16
@@ -273,6 +274,15 @@ def test_axpy_binary32_alpha_exact_path(k, mode):
     for alpha in (1.5, 0.5, 3.0):
         got = run_axpy(n, alpha, xi, f, 1, yi, f, 1, mode)
         check_axpy(got, n, alpha, xi, f, 1, yi, f, 1, mode)
+    # binary32 alphas with long expansions, and y within 2^-30 relative of -alpha x (near-cancellation:
+    # the exact sum is far below the terms, so the decision has to see the small error terms)
+    for alpha in (float(np.float32(0.1)), float(np.float32(1 / 3)), float(np.float32(12345.678))):
+        yc = -alpha * xv * (1 + np.ldexp(g.integers(-500, 500, n).astype(np.float64), -30))
+        ycs = _stream(yc, f)
+        got = run_axpy(n, alpha, xs, f, 1, ycs, f, 1, mode)
+        check_axpy(got, n, alpha, xs, f, 1, ycs, f, 1, mode)
+        got = run_axpy(n, alpha, xs, f, 1, ys, f, 1, mode)
+        check_axpy(got, n, alpha, xs, f, 1, ys, f, 1, mode)
 
 
 @pytest.mark.parametrize("k", [2, 3, 4])
