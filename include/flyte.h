@@ -293,6 +293,25 @@ flyte_status flyte_batch_launch(void* ws, cudaStream_t stream);
 flyte_status flyte_batch_autotune(void* ws, size_t ws_bytes, cudaStream_t stream);
 size_t flyte_batch_autotune_bytes(void);
 
+/* Tune the same table, and the number of resident blocks per SM of the
+ * persistent launch, on the caller's own batch (the GPU counterpart of the
+ * paper's unrolling study, Sec. 6, on the workload itself): first the
+ * resident blocks per SM, then the tile size of every (operation, k, base)
+ * present in jobs, each candidate timed as the whole batch (prepare, one
+ * untimed and three timed launches); a candidate is kept when it is at least
+ * 1 % faster.  Tile candidates: 16384..262144 elements (unpack, dot, axpy),
+ * 4..32 rows (gemv N), 128..512 rows per 1024-column block (gemv T); those
+ * whose tables do not fit in ws_bytes are skipped.  ws: device, 256-byte
+ * aligned.  The jobs run several times, so in-place outputs (axpy y) change:
+ * tune on scratch copies or re-initialise them.  Synchronous. */
+flyte_status flyte_batch_autotune_jobs(const flyte_job* jobs, int32_t njobs, void* ws, size_t ws_bytes,
+                                       cudaStream_t stream);
+
+/* The current tile size of (op, f) in the table (elements, or rows for gemv), or -1 for an
+ * invalid pair; and the resident blocks per SM the persistent launch uses. */
+int64_t flyte_batch_tile_size(int32_t op, flyte_fmt f);
+int32_t flyte_batch_resident_blocks(void);
+
 /* ---- helpers ---------------------------------------------------------------- */
 
 /* Scratch bytes an operation needs for the given sizes: op is "dot",

@@ -256,6 +256,21 @@ flyte_status flyte_batch_autotune(void* ws, size_t ws_bytes, cudaStream_t stream
 
 size_t flyte_batch_autotune_bytes(void) { return batch_autotune_bytes(); }
 
+flyte_status flyte_batch_autotune_jobs(const flyte_job* jobs, int32_t njobs, void* ws, size_t ws_bytes,
+                                       cudaStream_t stream) {
+  g_error[0] = 0;
+  if (njobs < 0 || (njobs > 0 && jobs == nullptr)) return invalid("jobs");
+  if (ws == nullptr || reinterpret_cast<uintptr_t>(ws) % 256 != 0) {
+    set_error("batch autotune: a 256-byte aligned workspace is required");
+    return FLYTE_ERR_WORKSPACE;
+  }
+  return batch_autotune_jobs(jobs, njobs, ws, ws_bytes, stream);
+}
+
+int64_t flyte_batch_tile_size(int32_t op, flyte_fmt f) { return batch_tile_size(op, f); }
+
+int32_t flyte_batch_resident_blocks(void) { return batch_resident_blocks(); }
+
 size_t flyte_workspace_bytes(const char* op, int64_t m, int64_t n, int64_t k_, flyte_fmt f) {
   (void)k_;
   if (!op || m < 0 || n < 0 || k_ < 0) return size_t(-1);

@@ -129,6 +129,17 @@ __device__ __forceinline__ bool axpy_exact_f32(uint64_t ux, uint64_t uy, float a
   return axpy_decide<K, MODE, false>(h, l, t2, 0.f, SplitRest{}, code) && ok;
 }
 
+// scal, alpha a binary32 number af: s = af x = p + e exactly (TwoProd), |e| <= ulp(p) / 2, so
+// (h, l, t2) = (p, e, 0) meets the premises of axpy_decide.
+template <int K, int MODE>
+__device__ __forceinline__ bool scal_exact_f32(uint64_t ux, float af, uint64_t& code) {
+  float xf, unused;
+  const bool ok = dbl_to_pair<K>(uint32_t(ux >> 32), 0u, xf, unused);
+  const float p = __fmul_rn(af, xf);
+  const float e = __fmaf_rn(af, xf, -p);
+  return axpy_decide<K, MODE, false>(p, e, 0.f, 0.f, SplitRest{}, code) && ok;
+}
+
 // Any binary64 alpha inside the window, split as a1 = RN32(alpha), a2 = RN32(alpha - a1),
 // a3 = RN32(alpha - a1 - a2) (|alpha - a1 - a2 - a3| <= 2^-72 |alpha|).  With p + e1 = a1 x
 // (TwoProd), p2 = RN(a2 x) and eA + eB = e1 + p2 (TwoSum), the chain of the binary32 case runs on
@@ -180,13 +191,14 @@ __device__ __forceinline__ bool axpy_exact_f32x2(uint64_t ux, uint64_t uy, float
 // near-cancellations) matched the oracle on every decided element; on
 // N(0,1) data it sends 0.009 % (k = 5), 0.004 % (k = 6) and 0.23 % (k = 7) of
 // the elements to binary64.
-template <int K, int MODE>
+// HAS_Y = false: s = a x (scal), with yh = yl = 0 (the chain stays exact).
+template <int K, int MODE, bool HAS_Y = true>
 __device__ __forceinline__ bool axpy_exact_wide(uint64_t ux, uint64_t uy, float a, uint64_t& code) {
   static_assert(K >= 5 && K <= 7, "double-based k = 5..7");
   constexpr int m = 8 * K - 12;
-  float xh, xl, yh, yl;
+  float xh, xl, yh = 0.f, yl = 0.f;
   bool ok = dbl_to_pair<K>(uint32_t(ux >> 32), uint32_t(ux), xh, xl);
-  ok &= dbl_to_pair<K>(uint32_t(uy >> 32), uint32_t(uy), yh, yl);
+  if constexpr (HAS_Y) ok &= dbl_to_pair<K>(uint32_t(uy >> 32), uint32_t(uy), yh, yl);
   const float p1 = __fmul_rn(a, xh), e1 = __fmaf_rn(a, xh, -p1);
   const float p2 = __fmul_rn(a, xl), e2 = __fmaf_rn(a, xl, -p2);
   float s1, t1, s2, t2, s3, t3, s4, t4, h, l;

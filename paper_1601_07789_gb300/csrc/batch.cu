@@ -495,7 +495,7 @@ __device__ void gemv_t_tile(const JobDev& jd, int tile, int64_t r0, int64_t r1, 
 
 // ---- the persistent kernel ----------------------------------------------------------------
 
-__global__ void __launch_bounds__(kBThreads) batch_kernel(uint8_t* __restrict__ ws) {
+__global__ void __launch_bounds__(kBThreads, 4) batch_kernel(uint8_t* __restrict__ ws) {
   extern __shared__ __align__(16) float xs[];   // x1, x2 of the current gemv tile
   __shared__ int s_item, s_last;
   __shared__ double s_red[kBWarps];
@@ -706,7 +706,11 @@ flyte_status make_plan(const flyte_job* jobs, int njobs, Plan& p) {
   return FLYTE_OK;
 }
 
-int batch_blocks() {
+// Resident blocks per SM the persistent grid uses: the occupancy limit, or fewer when the
+// autotuner measured fewer to be faster (g_tuned_per_sm > 0).
+int g_tuned_per_sm = 0;
+
+int max_blocks_per_sm() {
   static int per_sm = -1;
   if (per_sm < 0) {
     int v = 0;
@@ -714,8 +718,16 @@ int batch_blocks() {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, batch_kernel, kBThreads, kBatchSmem) != cudaSuccess) v = 1;
     per_sm = v < 1 ? 1 : v;
   }
-  return per_sm * sm_count();
+  return per_sm;
 }
+
+int blocks_per_sm() {
+  const int mx = max_blocks_per_sm();
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tuned_per_sm > 0 && g_tuned_per_sm < mx ? g_tuned_per_sm : mx;
+}
+
+int batch_blocks() { return blocks_per_sm() * sm_count(); }
 
 }  // namespace
 
@@ -878,5 +890,93 @@ flyte_status batch_autotune(void* ws, size_t ws_bytes, cudaStream_t s) {
   cudaEventDestroy(e1);
   return result;
 }
+
+// Tuning on the caller's own batch: coordinate descent, first over the resident blocks per SM,
+// then over the tile size of every (operation, base, k) that occurs in the jobs, each candidate
+// timed as the whole batch (prepare, one untimed launch, three timed launches); a candidate is
+// kept only when it is at least 1 % faster than the best so far.
+flyte_status batch_autotune_jobs(const flyte_job* jobs, int njobs, void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (jobs == nullptr || njobs <= 0) return FLYTE_OK;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return cuda_status(cudaGetLastError(), "batch autotune");
+  flyte_status result = FLYTE_OK;
+  // time of the batch with the current table; +inf when it does not fit in ws
+  auto run = [&](float& ms) -> flyte_status {
+    ms = 1e30f;
+    Plan p;
+    flyte_status st = make_plan(jobs, njobs, p);
+    if (st != FLYTE_OK) return st;
+    if (size_t(p.bytes) > ws_bytes) return FLYTE_OK;
+    if ((st = batch_prepare(jobs, njobs, ws, ws_bytes, s)) != FLYTE_OK) return st;
+    if ((st = batch_launch(ws, s)) != FLYTE_OK) return st;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3; ++r)
+      if ((st = batch_launch(ws, s)) != FLYTE_OK) return st;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return cuda_status(cudaGetLastError(), "batch autotune");
+    cudaEventElapsedTime(&ms, e0, e1);
+    return FLYTE_OK;
+  };
+  float best = 1e30f;
+  result = run(best);
+  // resident blocks per SM
+  if (result == FLYTE_OK) {
+    const int mx = max_blocks_per_sm();
+    int keep = 0;
+    for (int b = mx - 1; b >= 1 && b >= mx - 2 && result == FLYTE_OK; --b) {
+      {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned_per_sm = b;
+      }
+      float ms;
+      result = run(ms);
+      if (ms < 0.99f * best) {
+        best = ms;
+        keep = b;
+      }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned_per_sm = keep;
+  }
+  // tile sizes of the (operation, base, k) present
+  bool seen[kNOps][2][9] = {};
+  for (int i = 0; i < njobs && result == FLYTE_OK; ++i) {
+    const flyte_job& j = jobs[i];
+    if (j.op < 0 || j.op >= kNOps || !valid_fmt(j.fx)) continue;
+    const flyte_fmt f = (j.op == FLYTE_JOB_AXPY) ? j.fy : j.fx;
+    if (!valid_fmt(f) || seen[j.op][f.base][f.k]) continue;
+    seen[j.op][f.base][f.k] = true;
+    const int64_t cs[5] = {16384, 32768, 65536, 131072, 262144};
+    const int64_t cr[4] = {4, 8, 16, 32};
+    const int64_t cc[3] = {128, 256, 512};
+    const bool gn = j.op == FLYTE_JOB_GEMV_N, gt = j.op == FLYTE_JOB_GEMV_T;
+    const int64_t* cand = gt ? cc : (gn ? cr : cs);
+    const int nc = gt ? 3 : (gn ? 4 : 5);
+    const int64_t cur = tile_for(j.op, f);
+    int64_t keep = cur;
+    for (int c = 0; c < nc && result == FLYTE_OK; ++c) {
+      if (cand[c] == cur) continue;
+      set_tile(j.op, f, cand[c]);
+      float ms;
+      result = run(ms);
+      if (ms < 0.99f * best) {
+        best = ms;
+        keep = cand[c];
+      }
+    }
+    set_tile(j.op, f, keep);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return result;
+}
+
+int64_t batch_tile_size(int op, flyte_fmt f) {
+  if (op < 0 || op >= kNOps || !valid_fmt(f)) return -1;
+  return tile_for(op, f);
+}
+
+int batch_resident_blocks() { return blocks_per_sm(); }
 
 }  // namespace flyte

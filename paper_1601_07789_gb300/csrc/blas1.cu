@@ -285,6 +285,42 @@ __global__ void __launch_bounds__(kThreads) scal_groups(uint8_t* __restrict__ X,
   }
 }
 
+// Double-based k = 2..7 with a binary32 alpha: the code of pack(RN64(alpha x)) decided in binary32
+// (scal_exact_f32, and axpy_exact_wide without y for k = 5..7), binary64 for a group that needs it;
+// for k = 5..7 one warp in FLYTE_AXPY_WIDE_DIV multiplies in binary64, as for axpy.
+template <int K, int MODE>
+__global__ void __launch_bounds__(kThreads) scal_groups_f32exact(uint8_t* __restrict__ X, int64_t ngrp,
+                                                                 double alpha) {
+  const float af = float(alpha);
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const bool wide64 = K >= 5 && ((threadIdx.x >> 5) % FLYTE_AXPY_WIDE_DIV) == 0;
+  for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngrp; g += stride) {
+    uint32_t wx[K], wo[K];
+    load_group_rw<K>(X + g * (4 * K), wx);
+#pragma unroll
+    for (int j = 0; j < K; ++j) wo[j] = 0;
+    uint64_t c[4];
+    bool ok = !wide64;
+#pragma unroll
+    for (int q = 0; q < 4 && !wide64; ++q) {
+      const uint64_t ux = extract_widened<FLYTE_F64, K>(wx, q);
+      if constexpr (K >= 5) {
+        ok &= axpy_exact_wide<K, MODE, false>(ux, 0, af, c[q]);
+      } else {
+        ok &= scal_exact_f32<K, MODE>(ux, af, c[q]);
+      }
+    }
+    if (!ok) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        c[q] = scal_one<FLYTE_F64, K>(extract_widened<FLYTE_F64, K>(wx, q), alpha, af, MODE);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) deposit_code<K>(wo, q, c[q]);
+    store_group<K>(X + g * (4 * K), wo);
+  }
+}
+
 template <int BASE, int K>
 __global__ void __launch_bounds__(kThreads) scal_generic(uint8_t* __restrict__ X, int64_t incx, int64_t first,
                                                          int64_t n, double alpha, int mode) {
@@ -394,7 +430,22 @@ flyte_status launch_scal(int64_t n, double alpha, void* x, flyte_fmt fx, int64_t
     int64_t first = 0;
     if (incx == 1 && aligned(x, group_bytes(K)) && n >= 4) {
       const int64_t ngrp = n / 4;
-      scal_groups<BASE, K><<<grid_for(ngrp, kThreads), kThreads, 0, s>>>(X, ngrp, alpha, mode);
+      bool done = false;
+      if constexpr (BASE == FLYTE_F64 && K >= 2 && K <= 7) {
+        if (std::fabs(alpha) >= 0x1p-40 && std::fabs(alpha) < 0x1p40 && double(float(alpha)) == alpha) {
+          const unsigned grid = grid_for(ngrp, kThreads);
+          switch (mode) {
+            case FLYTE_RNE: scal_groups_f32exact<K, FLYTE_RNE><<<grid, kThreads, 0, s>>>(X, ngrp, alpha); break;
+            case FLYTE_RTZ: scal_groups_f32exact<K, FLYTE_RTZ><<<grid, kThreads, 0, s>>>(X, ngrp, alpha); break;
+            case FLYTE_HALF_UP:
+              scal_groups_f32exact<K, FLYTE_HALF_UP><<<grid, kThreads, 0, s>>>(X, ngrp, alpha);
+              break;
+            default: scal_groups_f32exact<K, FLYTE_RTO><<<grid, kThreads, 0, s>>>(X, ngrp, alpha); break;
+          }
+          done = true;
+        }
+      }
+      if (!done) scal_groups<BASE, K><<<grid_for(ngrp, kThreads), kThreads, 0, s>>>(X, ngrp, alpha, mode);
       FLYTE_TRY_LAUNCH("scal");
       first = ngrp * 4;
     }

@@ -385,5 +385,8 @@ flyte_status batch_prepare(const flyte_job* jobs, int njobs, void* ws, size_t ws
 flyte_status batch_launch(void* ws, cudaStream_t s);
 size_t batch_autotune_bytes();
 flyte_status batch_autotune(void* ws, size_t ws_bytes, cudaStream_t s);
+flyte_status batch_autotune_jobs(const flyte_job* jobs, int njobs, void* ws, size_t ws_bytes, cudaStream_t s);
+int64_t batch_tile_size(int op, flyte_fmt f);
+int batch_resident_blocks();
 
 }  // namespace flyte

@@ -29,7 +29,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "l
 EXPORTS = ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_scal", "flyte_gemv",
            "flyte_gemv_packed_y", "flyte_gemv_static", "flyte_gemm", "flyte_gemm_packed_c",
            "flyte_refine_jacobi", "flyte_batch_prepare", "flyte_batch_workspace_bytes", "flyte_batch_launch",
-           "flyte_batch_autotune", "flyte_batch_autotune_bytes", "flyte_workspace_bytes",
+           "flyte_batch_autotune", "flyte_batch_autotune_bytes", "flyte_batch_autotune_jobs",
+           "flyte_batch_tile_size", "flyte_batch_resident_blocks", "flyte_workspace_bytes",
            "flyte_last_error_string", "flyte_version")
 
 
@@ -103,10 +104,15 @@ def lib() -> ctypes.CDLL:
             L.flyte_batch_autotune.argtypes = [vp, sz, vp]
             L.flyte_batch_autotune_bytes.argtypes = []
             L.flyte_batch_autotune_bytes.restype = sz
+            L.flyte_batch_autotune_jobs.argtypes = [ctypes.POINTER(Job), i32, vp, sz, vp]
+            L.flyte_batch_tile_size.argtypes = [i32, Fmt]
+            L.flyte_batch_tile_size.restype = i64
+            L.flyte_batch_resident_blocks.argtypes = []
+            L.flyte_batch_resident_blocks.restype = i32
             for name in ("flyte_pack", "flyte_unpack", "flyte_dot", "flyte_axpy", "flyte_scal",
                          "flyte_gemv", "flyte_gemv_packed_y", "flyte_gemv_static", "flyte_gemm",
                          "flyte_gemm_packed_c", "flyte_refine_jacobi", "flyte_batch_prepare",
-                         "flyte_batch_launch", "flyte_batch_autotune"):
+                         "flyte_batch_launch", "flyte_batch_autotune", "flyte_batch_autotune_jobs"):
                 getattr(L, name).restype = i32
             L.flyte_workspace_bytes.argtypes = [ctypes.c_char_p, i64, i64, i64, Fmt]
             L.flyte_workspace_bytes.restype = sz
@@ -336,6 +342,29 @@ def batch_prepare(jobs, ws: torch.Tensor | None = None, device=None, stream=None
 def batch_launch(ws: torch.Tensor, stream=None) -> None:
     """Run a prepared batch (one persistent kernel; capturable in a CUDA graph)."""
     _check(lib().flyte_batch_launch(_ptr(ws), _stream(stream)))
+
+
+def batch_autotune_jobs(jobs, ws: torch.Tensor | None = None, device=None, stream=None) -> None:
+    """Tune the tile table and the resident blocks per SM on this batch of jobs (see
+    flyte_batch_autotune_jobs: in-place outputs such as axpy y are changed)."""
+    arr = (Job * len(jobs))(*jobs)
+    nbytes = 0
+    # the tables of the smallest tiles tried take at most about 4x the current ones; candidates
+    # that do not fit are skipped
+    cur = lib().flyte_batch_workspace_bytes(arr, len(jobs))
+    if cur != ctypes.c_size_t(-1).value:
+        nbytes = 16 * cur + (1 << 20)
+    if ws is None or ws.numel() < nbytes:
+        ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device or "cuda")
+    _check(lib().flyte_batch_autotune_jobs(arr, len(jobs), _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def batch_tile_size(op: int, f) -> int:
+    return int(lib().flyte_batch_tile_size(op, fmt(f)))
+
+
+def batch_resident_blocks() -> int:
+    return int(lib().flyte_batch_resident_blocks())
 
 
 def batch_autotune(device=None, stream=None) -> None:

@@ -176,11 +176,12 @@ def gemm_operands_f64(M: int, N: int, K: int, seed_a: int = 5, seed_b: int = 6):
     return A, B
 
 
-def refine_system(n: int, seed_g: int = 8, seed_b: int = 9):
-    """Diagonally dominant system of the refinement workload: A = G / sqrt(n) + n I with G N(0,1)
-    (row-major float64), and b N(0,1)."""
+def refine_system(n: int, seed_g: int = 8, seed_b: int = 9, diag: float | None = None):
+    """Diagonally dominant system of the refinement workload: A = G / sqrt(n) + d I with G N(0,1)
+    (row-major float64), d = n unless given (d = 10: a Jacobi contraction of about 1/10 per sweep),
+    and b N(0,1)."""
     A = rng(seed_g).standard_normal((n, n)) / np.sqrt(n)
-    A[np.arange(n), np.arange(n)] += n
+    A[np.arange(n), np.arange(n)] += n if diag is None else diag
     b = rng(seed_b).standard_normal(n)
     return A, b
 

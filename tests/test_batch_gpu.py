@@ -205,6 +205,27 @@ def test_batch_autotune_then_run():
     b.check()
 
 
+def test_batch_autotune_on_the_job_mix():
+    """flyte_batch_autotune_jobs times candidates on the caller's own batch; afterwards the table holds
+    candidate sizes, the persistent launch at least one block per SM, and the batch stays exact."""
+    specs = [s for s in inputs.batch_specs(48, seed=21, len_range=(1e3, 3e5), side_range=(64, 1500))]
+    tune = Batch(specs, seed=22)
+    flyte.batch_autotune_jobs(tune.jobs)
+    assert flyte.batch_resident_blocks() >= 1
+    for sp in specs:
+        f = (sp["k"], sp["base"])
+        t = flyte.batch_tile_size(sp["op"], f)
+        allowed = {0: {16384, 32768, 65536, 131072, 262144}, 1: {16384, 32768, 65536, 131072, 262144},
+                   2: {16384, 32768, 65536, 131072, 262144}, 3: {4, 8, 16, 32}, 4: {128, 256, 512}}[sp["op"]]
+        assert t in allowed, (sp, t)
+    assert flyte.batch_tile_size(9, (4, 1)) == -1
+    b = Batch(specs, seed=23)                      # fresh data: the tuning runs changed the axpy outputs
+    ws = flyte.batch_prepare(b.jobs)
+    flyte.batch_launch(ws)
+    sync()
+    b.check()
+
+
 def test_batch_config5_sizes_autotuned_tiles():
     """The same jobs after flyte_batch_autotune has filled the tile table."""
     flyte.batch_autotune()

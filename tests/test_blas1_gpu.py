@@ -230,6 +230,27 @@ def test_scal_sizes(f, mode):
         check_scal(got, n, -0.1234567890123, xs, f, 1, mode)
 
 
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("mode", MODES)
+def test_scal_binary32_alpha_exact_path(k, mode):
+    """A binary32 alpha takes the binary32 decision for double-based k = 2..7 (alpha x = p + e exactly,
+    and for k >= 5 the pairs of the wide axpy without y): bit-exact against the oracle on N(0,1), short
+    integers (exact products and ties) and out-of-window values (binary64 fallback)."""
+    f = (k, 1)
+    g = np.random.default_rng(70 + k)
+    n = 1 << 15
+    xv = g.standard_normal(n)
+    xv[3::17] *= 2.0 ** g.integers(-60, 60, xv[3::17].size)
+    xv[5::19] = 0.0
+    xs = _stream(xv, f)
+    xi = _stream(g.integers(-4096, 4096, n).astype(np.float64) / 8.0, f)
+    for alpha in (1.5, -2.0, float(np.float32(0.1)), float(np.float32(1 / 3)), float(np.float32(12345.678)),
+                  2.0 ** -30):
+        for data in (xs, xi):
+            got = run_scal(n, alpha, data, f, 1, mode)
+            check_scal(got, n, alpha, data, f, 1, mode)
+
+
 def test_scal_config_mixture_and_paths():
     """The 1M double mixture (specials included) at k = 3, 4, 5, and strided / offset streams."""
     n = 1 << 20

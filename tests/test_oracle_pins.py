@@ -516,6 +516,25 @@ def test_refine_converges_to_the_solution(k):
     assert np.linalg.norm(x - xs) <= 1.01 * np.linalg.norm(b - A @ x) / smin + 1e-15 * np.linalg.norm(xs)
 
 
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_refine_harder_system_converges(k):
+    """With diagonal 10 (Jacobi contraction about 1/10 per sweep) and 8 sweeps per correction the
+    refinement still reaches 1e-12; its x agrees with LAPACK's solve; k = 3, whose stored entries err
+    by up to 2^-13 relative, needs at least as many corrections as k = 5."""
+    n = 256
+    g = np.random.default_rng(40 + k)
+    A = g.standard_normal((n, n)) / np.sqrt(n) + 10.0 * np.eye(n)
+    b = g.standard_normal(n)
+    Ak = oracle.pack(A.reshape(-1), 1, k)
+    x, it, rel = oracle.refine_jacobi(n, A, Ak, (1, k), b, np.zeros(n), 1e-12, 40, 8)
+    assert rel <= 1e-12 and 1 <= it <= 40
+    xs = np.linalg.solve(A, b)
+    smin = np.linalg.svd(A, compute_uv=False)[-1]
+    assert np.linalg.norm(x - xs) <= 1.01 * np.linalg.norm(b - A @ x) / smin + 1e-15 * np.linalg.norm(xs)
+    it5 = oracle.refine_jacobi(n, A, oracle.pack(A.reshape(-1), 1, 5), (1, 5), b, np.zeros(n), 1e-12, 40, 8)[1]
+    assert it >= it5 if k == 3 else True
+
+
 def test_refine_one_step_semantics():
     """max_outer = 1 with one sweep is exactly x1 = x0 + D^-1 (b - A x0), written out in NumPy; with
     tol = inf nothing is corrected; the contraction per correction follows the stored precision."""

@@ -46,6 +46,25 @@ def test_refine_matches_oracle(k, n):
     assert np.linalg.norm(xg - xo) <= 1.01 * (rg + ro) / smin + 1e-15 * np.linalg.norm(xo)
 
 
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_refine_harder_system_matches_oracle(k):
+    """A = G/sqrt(n) + 10 I with 8 sweeps per correction: the stored precision limits each correction
+    (k = 3 needs more of them); GPU and oracle take the same steps and reach the same solution."""
+    n = 1024
+    A, b = inputs.refine_system(n, 31, 32, diag=10.0)
+    Ak = oracle.pack(A.reshape(-1), 1, k)
+    x0 = np.zeros(n)
+    xg, itg, relg = gpu_refine(A, Ak, (k, 1), b, x0, 1e-12, 40, 8)
+    xo, ito, relo = oracle.refine_jacobi(n, A, Ak, (1, k), b, x0, 1e-12, 40, 8)
+    assert relg <= 1e-12 and relo <= 1e-12
+    assert itg == ito
+    smin = np.linalg.svd(A, compute_uv=False)[-1]
+    rg = np.linalg.norm(b - A @ xg)
+    ro = np.linalg.norm(b - A @ xo)
+    assert rg <= 2e-12 * np.linalg.norm(b)
+    assert np.linalg.norm(xg - xo) <= 1.01 * (rg + ro) / smin + 1e-15 * np.linalg.norm(xo)
+
+
 def test_refine_fixed_steps_and_edges():
     """A fixed number of steps (tol = 0) from a nonzero guess, inner = 1 and 3; tol = inf does nothing."""
     n = 777
