@@ -30,6 +30,12 @@ constexpr int kThreads = 256;
 #ifndef FLYTE_AXPY_WIDE_DIV
 #define FLYTE_AXPY_WIDE_DIV 3          // k = 5..7 axpy: one warp in this many runs the binary64 fma
 #endif
+// k = 5..7 scal: one warp in this many multiplies in binary64.  The binary32 side of scal has no y
+// to carry, so fewer warps on the fp64 pipe balance it (measured at 2^28 elements, k = 5 / 6 / 7:
+// one in four 3.32 / 4.19 / 4.44 TB/s, one in three 3.18 / 3.84 / 4.29, one in five 3.35 / 4.09 / 4.44)
+#ifndef FLYTE_SCAL_WIDE_DIV
+#define FLYTE_SCAL_WIDE_DIV 4
+#endif
 constexpr int kDotMaxBlocks = 2048;   // fixed, so the workspace size does not depend on the device
 constexpr int kHdrBytes = 256;
 
@@ -287,13 +293,13 @@ __global__ void __launch_bounds__(kThreads) scal_groups(uint8_t* __restrict__ X,
 
 // Double-based k = 2..7 with a binary32 alpha: the code of pack(RN64(alpha x)) decided in binary32
 // (scal_exact_f32, and axpy_exact_wide without y for k = 5..7), binary64 for a group that needs it;
-// for k = 5..7 one warp in FLYTE_AXPY_WIDE_DIV multiplies in binary64, as for axpy.
+// for k = 5..7 one warp in FLYTE_SCAL_WIDE_DIV multiplies in binary64, as axpy does.
 template <int K, int MODE>
 __global__ void __launch_bounds__(kThreads) scal_groups_f32exact(uint8_t* __restrict__ X, int64_t ngrp,
                                                                  double alpha) {
   const float af = float(alpha);
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-  const bool wide64 = K >= 5 && ((threadIdx.x >> 5) % FLYTE_AXPY_WIDE_DIV) == 0;
+  const bool wide64 = K >= 5 && ((threadIdx.x >> 5) % FLYTE_SCAL_WIDE_DIV) == 0;
   for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ngrp; g += stride) {
     uint32_t wx[K], wo[K];
     load_group_rw<K>(X + g * (4 * K), wx);
