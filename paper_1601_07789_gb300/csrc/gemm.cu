@@ -261,7 +261,7 @@ __device__ __forceinline__ void store_c(double* C, const COut& co, int64_t idx, 
 // blockIdx.x + gridDim.x, ... in groups of kGroupRows tile rows (column by
 // column inside a group, so that concurrently running CTAs share A and B
 // tiles in L2).  Warps [0, E): epilogue; warp E: TMA producer; warp E + 1:
-// MMA issuer and TMEM owner.  The stage ring and the two TMEM chunk buffers
+// MMA issuer and TMEM owner.  The stage ring and the TMEM chunk buffers
 // run on across tiles, so the next tile's loads and MMAs overlap this tile's
 // C store.
 //
