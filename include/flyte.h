@@ -277,10 +277,11 @@ flyte_status flyte_batch_prepare(const flyte_job* jobs, int32_t njobs, void* ws,
                                  cudaStream_t stream);
 size_t flyte_batch_workspace_bytes(const flyte_job* jobs, int32_t njobs);
 
-/* Run a prepared batch: one persistent kernel (one block per resident slot)
- * whose blocks take tiles from a counter in ws until none are left; a dot's
- * partial sums are added in tile order by the block that finishes its last
- * tile, so results are deterministic.  Asynchronous, allocates nothing and
+/* Run a prepared batch: a small kernel that splits the x of every gemv 'N'
+ * job once into its binary32 pair (into ws), then one persistent kernel (one
+ * block per resident slot) whose blocks take tiles from a counter in ws
+ * until none are left; a dot's partial sums are added in tile order by the
+ * block that finishes its last tile, so results are deterministic.  Asynchronous, allocates nothing and
  * may be captured in a CUDA graph and replayed (ws must stay untouched
  * between prepare and the last replay).  Jobs in one batch must not write
  * memory that another job of the batch reads or writes. */

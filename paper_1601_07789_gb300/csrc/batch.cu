@@ -51,11 +51,12 @@ struct JobDev {
   int32_t done_base;                          // first completion counter of the job
   int32_t ua;                                 // dot/gemv: groups not 4k-byte aligned (funnel-shift loads)
   int32_t pad;
+  int64_t xsplit;                             // gemv N (double-word path): address of its x1, x2 in ws
 };
 
 struct Header {
   int32_t njobs, nitems, ndone, pad;
-  int64_t off_jobs, off_items, off_parts, off_done;
+  int64_t off_jobs, off_items, off_parts, off_done, off_xs;
   int32_t counter;   // next tile to take
   int32_t exited;    // blocks that have finished
 };
@@ -358,6 +359,16 @@ __device__ void split_x(const double* __restrict__ x, int64_t len, float* x1, fl
   }
 }
 
+// Elements [b, e) of a job's split x (x1 at xg, x2 at xg + len, written by batch_split_x) into the
+// tile's shared x1, x2.
+__device__ __forceinline__ void stage_x(const float* __restrict__ xg, int64_t len, int64_t b, int64_t e, float* x1,
+                                        float* x2) {
+  for (int64_t j = b + threadIdx.x; j < e; j += kBThreads) {
+    x1[j - b] = xg[j];
+    x2[j - b] = xg[len + j];
+  }
+}
+
 template <int BASE, int K>
 __device__ __forceinline__ void fold_elem(typename Native<BASE>::bits u, float x1, float x2, DW& acc, bool& ok) {
   float hi, lo, p, e;
@@ -379,7 +390,7 @@ __device__ void gemv_n_tile(const JobDev& jd, int64_t r0, int64_t r1, float* x1,
   double* y = static_cast<double*>(jd.j.y);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (jd.fast) {
-    split_x(x, n, x1, x2);
+    stage_x(reinterpret_cast<const float*>(jd.xsplit), n, 0, n, x1, x2);
     __syncthreads();
   }
   for (int64_t r = r0 + warp; r < r1; r += kBWarps) {
@@ -446,7 +457,31 @@ __device__ void gemv_t_tile(const JobDev& jd, int tile, int64_t r0, int64_t r1, 
     for (int q = 0; q < 4; ++q) dw_zero(acc[0][q]), dw_zero(acc[1][q]);
     const uint8_t* colp = A + c * K;
     int since = 0;
-    for (int64_t i = r0; i < r1; ++i) {
+    int64_t i = r0;
+    // two rows per step, both loads in flight before the folds (the chains, their order and the
+    // fold points are those of the one-row loop below: fold_rows is even)
+    for (; i + 1 < r1; i += 2) {
+      uint32_t w0[K], w1[K];
+      load_group_any<K>(colp + i * n * K, w0, jd.ua);
+      load_group_any<K>(colp + (i + 1) * n * K, w1, jd.ua);
+      const float a1 = x1[i - r0], a2 = x2[i - r0], b1 = x1[i + 1 - r0], b2 = x2[i + 1 - r0];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) fold_elem<BASE, K>(extract_widened<BASE, K>(w0, q), a1, a2, acc[i & 1][q], ok);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        fold_elem<BASE, K>(extract_widened<BASE, K>(w1, q), b1, b2, acc[(i + 1) & 1][q], ok);
+      since += 2;
+      if (since == jd.fold_rows) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          v[q] += dw_value(acc[0][q]) + dw_value(acc[1][q]);
+          dw_zero(acc[0][q]);
+          dw_zero(acc[1][q]);
+        }
+        since = 0;
+      }
+    }
+    for (; i < r1; ++i) {
       uint32_t w[K];
       load_group_any<K>(colp + i * n * K, w, jd.ua);
       const float a1 = x1[i - r0], a2 = x2[i - r0];
@@ -490,6 +525,23 @@ __device__ void gemv_t_tile(const JobDev& jd, int tile, int64_t r0, int64_t r1, 
       for (int r = 0; r < nrc; ++r) t += __ldcg(col + int64_t(r) * (4 * kBThreads) + q);
       y[c + q] = gemv_epilogue(t, jd.j.alpha, jd.j.beta, y + c + q);
     }
+  }
+}
+
+// ---- x of the gemv jobs, split once per launch -------------------------------------------
+
+// x1, x2 of every gemv N job on the double-word path, into the workspace (x1 then x2, n each),
+// before the persistent kernel: its row tiles copy them instead of each splitting the whole x again
+// (the splitting runs on the binary64 pipe; tiles of 16-32 rows repeated it for every tile).  'T'
+// tiles split only their own rows of x, a small share of their work, and keep doing so.
+__global__ void __launch_bounds__(kBThreads) batch_split_x(uint8_t* __restrict__ ws) {
+  const Header* h = reinterpret_cast<const Header*>(ws);
+  const JobDev* jobs = reinterpret_cast<const JobDev*>(ws + h->off_jobs);
+  for (int i = blockIdx.x; i < h->njobs; i += gridDim.x) {
+    const JobDev& jd = jobs[i];
+    if (jd.j.op != FLYTE_JOB_GEMV_N || !jd.fast || jd.tiles == 0) continue;
+    float* x1 = reinterpret_cast<float*>(jd.xsplit);
+    split_x(jd.j.xv, jd.j.n, x1, x1 + jd.j.n);
   }
 }
 
@@ -702,7 +754,15 @@ flyte_status make_plan(const flyte_job* jobs, int njobs, Plan& p) {
   p.hdr.off_items = p.hdr.off_jobs + up256(int64_t(sizeof(JobDev)) * njobs);
   p.hdr.off_parts = p.hdr.off_items + up256(int64_t(sizeof(Item)) * int64_t(p.items.size()));
   p.hdr.off_done = p.hdr.off_parts + up256(8 * p.nparts);
-  p.bytes = p.hdr.off_done + up256(4 * int64_t(p.ndone));
+  // x1, x2 (binary32) of each gemv N job on the double-word path
+  int64_t xs = 0;
+  for (JobDev& d : p.jobs) {
+    if (d.j.op != FLYTE_JOB_GEMV_N || !d.fast || d.tiles == 0) continue;
+    d.xsplit = xs;   // an offset from off_xs here; flyte_batch_prepare makes it an address
+    xs += (8 * d.j.n + 15) / 16 * 16;
+  }
+  p.hdr.off_xs = p.hdr.off_done + up256(4 * int64_t(p.ndone));
+  p.bytes = p.hdr.off_xs + up256(xs);
   return FLYTE_OK;
 }
 
@@ -745,6 +805,11 @@ flyte_status batch_prepare(const flyte_job* jobs, int njobs, void* ws, size_t ws
     set_error("batch: workspace of %lld bytes (256-byte aligned) required", (long long)p.bytes);
     return FLYTE_ERR_WORKSPACE;
   }
+  // the gemv N jobs' split-x slots as addresses inside ws
+  for (JobDev& d : p.jobs) {
+    if (d.j.op == FLYTE_JOB_GEMV_N && d.fast && d.tiles > 0)
+      d.xsplit = int64_t(reinterpret_cast<uintptr_t>(ws)) + p.hdr.off_xs + d.xsplit;
+  }
   // header, jobs and tiles; the dot partials need no initial value; done counters start at 0
   std::vector<uint8_t> host(size_t(p.bytes), 0);
   std::memcpy(host.data(), &p.hdr, sizeof(Header));
@@ -762,6 +827,8 @@ flyte_status batch_launch(void* ws, cudaStream_t s) {
     return FLYTE_ERR_WORKSPACE;
   }
   const int blocks = batch_blocks();
+  batch_split_x<<<2 * sm_count(), kBThreads, 0, s>>>(static_cast<uint8_t*>(ws));
+  FLYTE_TRY_LAUNCH("batch");
   batch_kernel<<<blocks, kBThreads, kBatchSmem, s>>>(static_cast<uint8_t*>(ws));
   FLYTE_TRY_LAUNCH("batch");
   return FLYTE_OK;
