@@ -50,7 +50,7 @@ struct JobDev {
   int32_t row_chunks;                         // gemv 'T': row chunks per column block
   int32_t done_base;                          // first completion counter of the job
   int32_t ua;                                 // dot/gemv: groups not 4k-byte aligned (funnel-shift loads)
-  int32_t pad;
+  int32_t tgroups;                            // gemv 'T': row groups per tile (1, 2, 4, 8, 16)
   int64_t xsplit;                             // gemv N (double-word path): address of its x1, x2 in ws
 };
 
@@ -442,12 +442,18 @@ __device__ void gemv_t_tile(const JobDev& jd, int tile, int64_t r0, int64_t r1, 
   double* y = static_cast<double*>(jd.j.y);
   const int nrc = jd.row_chunks;
   const int cb = tile / nrc, rc = tile % nrc;
-  const int64_t c0 = int64_t(cb) * (4 * kBThreads);
+  // G row groups of nthr threads: a narrow matrix (n below 4 x 256 columns) keeps every thread busy
+  // by giving each group an even share of the chunk's rows; group 0 adds the groups' sums in order
+  const int G = jd.tgroups, nthr = kBThreads / G;
+  const int tg = threadIdx.x / nthr, tc = threadIdx.x % nthr;
+  const int64_t c0 = int64_t(cb) * (4 * nthr);
   if (jd.fast) {
     split_x(x + r0, r1 - r0, x1, x2);
     __syncthreads();
   }
-  const int64_t c = c0 + 4 * threadIdx.x;
+  const int64_t sub = ((r1 - r0 + G - 1) / G + 1) & ~int64_t(1);
+  const int64_t ra = min(r1, r0 + tg * sub), rb = min(r1, ra + sub);
+  const int64_t c = c0 + 4 * tc;
   const int nc = int(max(int64_t(0), min(int64_t(4), n - c)));
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   bool ok = jd.fast && nc == 4;
@@ -457,10 +463,10 @@ __device__ void gemv_t_tile(const JobDev& jd, int tile, int64_t r0, int64_t r1, 
     for (int q = 0; q < 4; ++q) dw_zero(acc[0][q]), dw_zero(acc[1][q]);
     const uint8_t* colp = A + c * K;
     int since = 0;
-    int64_t i = r0;
+    int64_t i = ra;
     // two rows per step, both loads in flight before the folds (the chains, their order and the
     // fold points are those of the one-row loop below: fold_rows is even)
-    for (; i + 1 < r1; i += 2) {
+    for (; i + 1 < rb; i += 2) {
       uint32_t w0[K], w1[K];
       load_group_any<K>(colp + i * n * K, w0, jd.ua);
       load_group_any<K>(colp + (i + 1) * n * K, w1, jd.ua);
@@ -481,7 +487,7 @@ __device__ void gemv_t_tile(const JobDev& jd, int tile, int64_t r0, int64_t r1, 
         since = 0;
       }
     }
-    for (; i < r1; ++i) {
+    for (; i < rb; ++i) {
       uint32_t w[K];
       load_group_any<K>(colp + i * n * K, w, jd.ua);
       const float a1 = x1[i - r0], a2 = x2[i - r0];
@@ -506,20 +512,35 @@ __device__ void gemv_t_tile(const JobDev& jd, int tile, int64_t r0, int64_t r1, 
   if (!ok) {
     for (int q = 0; q < nc; ++q) {
       double s2 = 0.0;
-      for (int64_t i = r0; i < r1; ++i)
+      for (int64_t i = ra; i < rb; ++i)
         s2 = fma(code_to_double<BASE, K>(load_code_bytes<K>(A + (i * n + c + q) * K)), x[i], s2);
       v[q] = s2;
     }
   }
-  double* mine = parts + jd.part_base + (int64_t(cb) * nrc + rc) * (4 * kBThreads) + 4 * threadIdx.x;
-  for (int q = 0; q < nc; ++q) mine[q] = v[q];
+  if (G > 1) {
+    // the groups' sums through shared memory (above the tile's x1: at most 1024 rows), in group order
+    double* pp = reinterpret_cast<double*>(x1 + 1024);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pp[4 * threadIdx.x + q] = v[q];
+    __syncthreads();
+    if (tg == 0) {
+      for (int g2 = 1; g2 < G; ++g2) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] += pp[4 * (g2 * nthr + tc) + q];
+      }
+    }
+  }
+  double* mine = parts + jd.part_base + (int64_t(cb) * nrc + rc) * (4 * kBThreads) + 4 * tc;
+  if (tg == 0)
+    for (int q = 0; q < nc; ++q) mine[q] = v[q];
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) *s_last = atomicAdd(&done[jd.done_base + cb], 1) == nrc - 1;
   __syncthreads();
-  if (*s_last) {
+  if (*s_last && tg == 0) {
     __threadfence();
-    const double* col = parts + jd.part_base + int64_t(cb) * nrc * (4 * kBThreads) + 4 * threadIdx.x;
+    const double* col = parts + jd.part_base + int64_t(cb) * nrc * (4 * kBThreads) + 4 * tc;
     for (int q = 0; q < nc; ++q) {
       double t = 0.0;
       for (int r = 0; r < nrc; ++r) t += __ldcg(col + int64_t(r) * (4 * kBThreads) + q);
@@ -698,11 +719,18 @@ flyte_status make_plan(const flyte_job* jobs, int njobs, Plan& p) {
         // into binary64 every fold rows; binary64 levels: the folds of a chunk, then the chunks in order
         const int64_t rows = std::max<int64_t>(4, tile);
         const int64_t nrc = (j.m + rows - 1) / rows;
-        const int64_t ncb = (j.n + 4 * kBThreads - 1) / (4 * kBThreads);
+        // threads per row group: 4 columns each, a power of two covering n (at least 16); the
+        // block's other threads take further shares of the chunk's rows (chunks of <= 1024 rows)
+        int64_t nthr = kBThreads;
+        while (rows <= 1024 && nthr > 16 && 4 * (nthr / 2) >= j.n) nthr /= 2;
+        const int64_t G = kBThreads / nthr;
+        d.tgroups = int32_t(G);
+        const int64_t ncb = (j.n + 4 * nthr - 1) / (4 * nthr);
         d.fast = 0;
         d.fold_rows = 64;
         for (int64_t f = 64; f >= 2; f /= 2) {
-          if (dw_bound_ok(j.m, f / 2 + 1, 2 * (rows / f) + 4 + nrc, 14)) {
+          // + G: the groups' sums added in binary64
+          if (dw_bound_ok(j.m, f / 2 + 1, 2 * (rows / f) + 4 + nrc + G, 14)) {
             d.fast = 1;
             d.fold_rows = int32_t(f);
             break;
