@@ -169,6 +169,32 @@ def test_batch_misaligned_and_edges():
                                        xv=b.dev[0]["x"])])   # gemv side above the batch limit
 
 
+# 'T' jobs narrower than 1024 columns cut each tile's rows among G thread groups (G = 16, 8, 4, 2, 1
+# here, one with a ragged last group) and 'N' jobs share an x split once per launch across many row
+# tiles (one on the double-word tree, one on the binary64 row sums): against the oracle, and a second
+# launch gives the same bits.
+NARROW = [{"op": 4, "k": k, "base": 1, "n": n, "m": 4096}
+          for k, n in ((3, 64), (5, 66), (4, 100), (6, 200), (2, 500), (7, 1000))] + [
+    {"op": 3, "k": 4, "base": 1, "n": 1500, "m": 3000},
+    {"op": 3, "k": 5, "base": 1, "n": 600, "m": 2000},
+]
+
+
+def test_batch_narrow_t_groups_and_split_x():
+    b = Batch(NARROW, seed=31)
+    ws = flyte.batch_prepare(b.jobs)
+    flyte.batch_launch(ws)
+    sync()
+    b.check(gemv_sample=300)
+    first = [d["y"].clone() for d in b.dev]
+    for i, s in enumerate(NARROW):
+        b.dev[i]["y"].copy_(torch.from_numpy(b.host[i]["y0"]))
+    flyte.batch_launch(ws)
+    sync()
+    for a, d in zip(first, b.dev):
+        assert torch.equal(a, d["y"])
+
+
 # The batched workload's own size distribution (vector lengths log-uniform in 10^3..10^6, gemv sides
 # log-uniform in 64..4096), plus jobs that reach the paths only large sides take: 'T' jobs several
 # 1024-column blocks wide and gemv jobs whose x (staged in shared memory) has 4096 entries.
