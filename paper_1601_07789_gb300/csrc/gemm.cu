@@ -174,13 +174,12 @@ struct GemmCfg {
   // kBufs chunks of one k-block (they are not preloaded, see below)
   static constexpr int kChunkBlocks = NP == 1 ? FLYTE_GEMM_CHUNK1 : 1;
   static constexpr bool kPreload = NP == 1;
-  // Columns per epilogue warp (32 rows each): a split format folds every
-  // k-block and needs the latency hiding of 16 warps (96 registers each);
-  // a one-part format folds every 4 k-blocks, and 8 warps (168 registers)
-  // keep its pair accumulators without spills (measured at 8192^3: 16 warps
-  // k = 3 269 / k = 4 215 TFLOP/s against 205 / 197 with 8; one part 662
-  // with 8 against 614 with 16)
-  static constexpr int kEpiCols = NP == 1 ? 64 : 32;
+  // Columns per epilogue warp (32 rows each): 8 warps of 168 registers keep
+  // their pair accumulators without spilling, where 16 warps of 96 spilled
+  // (measured at 8192^3 with the f32x2 fold and 16-column loads: k = 3 / 4
+  // 325 / 253 useful TFLOP/s against 314 / 243 with 16 warps; one part 662
+  // against 614 in the same comparison before the 16-column loads)
+  static constexpr int kEpiCols = 64;
   static constexpr int kLoadCols = 16;   // TMEM columns per tcgen05.ld (one-part: 16 against 8, 681 against 665 TFLOP/s at 8192^3)
   static constexpr int kEpiWarps = 4 * (BN / kEpiCols);
   static constexpr int kThreads = 32 * (kEpiWarps + 2);      // + producer warp + MMA warp
