@@ -2,21 +2,24 @@
 //
 // flyte_batch_prepare splits each job into tiles (a range of elements, a
 // block of gemv rows, or a block of gemv columns) and uploads a job table and
-// a tile table into the caller's workspace.  flyte_batch_launch starts one
-// persistent kernel of (SMs x resident blocks) blocks; each block repeatedly
+// a tile table into the caller's workspace.  flyte_batch_launch starts a
+// small kernel that splits the x of every gemv 'N' job into its binary32 pair
+// once, then one persistent kernel of (SMs x resident blocks) blocks; each
+// block repeatedly
 // takes the next tile from an atomic counter and runs it with all its
 // threads, so short and long jobs share the machine without a launch per
 // job.  A dot's tiles leave partial sums in the workspace; the block that
 // completes a dot's last tile adds them in tile order, so the result does not
 // depend on the schedule.  The last block to finish resets the counters, so
-// a launch is a single kernel and can be replayed from a CUDA graph.  The
-// kernel has no inter-block waits.
+// a launch can be replayed from a CUDA graph.  The kernels have no
+// inter-block waits.
 //
 // The arithmetic is that of the single-job kernels: exact widening and
 // integer narrowing (flyte_internal.cuh), double-word accumulation for
 // in-window data when the host has proven the error bound for the job
-// (dwacc.cuh), binary64 FMAs otherwise.  gemv splits x into binary32 pairs
-// once per tile in shared memory, which caps the batch gemv sides at 4096.
+// (dwacc.cuh), binary64 FMAs otherwise.  gemv tiles stage x as binary32
+// pairs in shared memory ('N' tiles copy the pair split once per launch, 'T'
+// tiles split their own rows), which caps the batch gemv sides at 4096.
 //
 // Tile sizes come from a per-(operation, base, k) table: built-in defaults,
 // replaced by the fastest candidates that flyte_batch_autotune measures.
