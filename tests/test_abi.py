@@ -76,3 +76,18 @@ def test_batch_job_layout_and_host_validation(lib):
     assert lib.flyte_batch_prepare(big, 1, None, 0, None) == 2     # gemv side above the batch limit
     ok = (flyte.Job * 1)(flyte.Job(0, 0, flyte.Fmt(3, 1), flyte.Fmt(3, 1), 0, 1000, 16, None, 16, None, 0.0, 0.0))
     assert 0 < lib.flyte_batch_workspace_bytes(ok, 1) < 4096
+
+
+def test_batch_plan_reserves_the_split_x_of_gemv_n_jobs(lib):
+    """The planner (host code) keeps a binary32 pair slot, 8 bytes per entry of x, for each gemv 'N' job
+    on the double-word path, split once per launch; a job too short for that path (binary64 row sums)
+    gets none."""
+    def ws(n, count):
+        jobs = (flyte.Job * count)(*[flyte.Job(3, 0, flyte.Fmt(4, 1), flyte.Fmt(4, 1), 64, n, 1, 1, 1, None, 1.0,
+                                               0.0) for _ in range(count)])
+        return lib.flyte_batch_workspace_bytes(jobs, count)
+
+    long_rows = ws(2048, 2) - ws(2048, 1)     # n = 2048: the double-word path
+    short_rows = ws(300, 2) - ws(300, 1)      # n = 300: too short for its bound
+    assert long_rows >= 8 * 2048
+    assert short_rows < 8 * 300               # its job and tile entries only, no x slot
